@@ -1,0 +1,131 @@
+/*
+ * lch.h - C ABI of the GB300 library for the transform in the Lin-Chung-Han
+ * polynomial basis over GF(2^r) and the Reed-Solomon erasure code built on it
+ * (S.-J. Lin, W.-H. Chung, Y. S. Han, "Novel Polynomial Basis and Its
+ * Application to Reed-Solomon Erasure Codes").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Field.     `field` is LCH_GF8 (r = 8, reduction polynomial
+ *            x^8+x^4+x^3+x^2+1) or LCH_GF16 (r = 16, x^16+x^12+x^3+x+1).
+ *            The paper's basis v_0..v_{r-1} (Sec. II.A) is taken to be the
+ *            polynomial basis v_j = x^j, so the point w_i is the field element
+ *            whose bit pattern is i and w_a + w_b = w_{a xor b}.
+ * Symbols.   A symbol is one shard: a row of `shard_bytes` bytes.  Each
+ *            element offset inside the shards is an independent column that
+ *            is transformed with the same factors.  GF(2^8) elements are
+ *            bytes; GF(2^16) elements are little-endian uint16 (bit b is the
+ *            coefficient of x^b).
+ * Buffers.   Every data pointer is a DEVICE pointer to `rows x shard_bytes`
+ *            bytes, row-major (row t starts at buf + t * shard_bytes), owned
+ *            by the caller, 16-byte aligned.  `shard_bytes` must be a nonzero
+ *            multiple of 16.
+ * Streams.   `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *            Every call only enqueues work on it and returns; results are
+ *            ready when the stream reaches that point.  The first call that
+ *            uses a field on a context builds that field's tables and
+ *            synchronises `stream` once.
+ * Errors.    Arguments are checked on the host before anything is enqueued;
+ *            a call that returns an error has modified no buffer.  Status 0 is
+ *            success; see lch_strerror() and lch_last_error() for the rest.
+ * Threads.   A context may be used from one host thread at a time.  Calls on
+ *            one context that run concurrently on different streams race on
+ *            the context's scratch memory; serialise them on one stream.
+ */
+#ifndef LCH_H
+#define LCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define LCH_API __attribute__((visibility("default")))
+#else
+#define LCH_API
+#endif
+
+/* Status codes. */
+#define LCH_OK 0
+#define LCH_EINVAL 1   /* an argument is out of range or misaligned */
+#define LCH_ETOOMANY 2 /* rs_decode: more than n - k erasures */
+#define LCH_ENOMEM 3   /* device or host allocation failed */
+#define LCH_ECUDA 4    /* a CUDA runtime call failed (see lch_last_error) */
+
+/* Fields. */
+#define LCH_GF8 8
+#define LCH_GF16 16
+
+typedef struct lch_ctx lch_ctx;
+
+/* Create a context bound to CUDA device `device`.  The context owns the
+ * per-field tables (built lazily) and a scratch area that grows on demand.
+ * On success *ctx receives the handle and LCH_OK is returned. */
+LCH_API int lch_ctx_create(lch_ctx **ctx, int device);
+
+/* Release a context and everything it owns.  Waits for the device first.
+ * NULL is ignored. */
+LCH_API void lch_ctx_destroy(lch_ctx *ctx);
+
+/* Forward transform Psi_h^l (Sec. III, the set Psi(0,0,l) of Sec. III.C).
+ * buf holds h rows: on entry row i is coefficient d_i of
+ * [D_h](x) = sum_i d_i X_i(x) (Def. 1); on return row c is [D_h](w_c + w_l).
+ * h: power of two, 1 <= h <= 2^r.  l: shift, 0 <= l < 2^r (any value; the
+ * encoder uses multiples of h).  In place. */
+LCH_API int lch_fft(lch_ctx *ctx, int field, uint32_t h, uint32_t l, void *buf, size_t shard_bytes,
+                    void *stream);
+
+/* Inverse transform (Psi_h^l)^{-1} (Sec. III.E): on entry row c holds the
+ * value at w_c + w_l, on return row i holds d_i.  Same arguments as
+ * lch_fft.  In place. */
+LCH_API int lch_ifft(lch_ctx *ctx, int field, uint32_t h, uint32_t l, void *buf, size_t shard_bytes,
+                     void *stream);
+
+/* Formal derivative in the basis (Sec. IV, eqs. D'_h(x)-2 and XDhx3): on
+ * entry buf holds the h coefficients of [D_h], on return the h coefficients
+ * of [D_h]' (the last one is always zero).  h: power of two, 1 <= h <= 2^r.
+ * In place; uses context scratch of h * shard_bytes bytes. */
+LCH_API int lch_derivative(lch_ctx *ctx, int field, uint32_t h, void *buf, size_t shard_bytes,
+                           void *stream);
+
+/* Systematic (n, k) Reed-Solomon encoding (Sec. V, Algorithm 1).
+ * shards holds n rows; rows 0..k-1 are the message m_0..m_{k-1} and are only
+ * read; rows k..n-1 are overwritten with F(w_k)..F(w_{n-1}), where F is the
+ * polynomial of degree < k with F(w_i) = m_i (eq. F(i)=m_i).
+ * n: power of two, 1 <= n <= 2^r.  1 <= k <= n.  When k is a power of two
+ * Algorithm 1 runs as printed; otherwise the parity rows are recovered as
+ * erasures of a codeword whose message rows are known (Algorithm 2 with
+ * E = {k..n-1}), which yields the same unique F.  Uses context scratch of
+ * up to 2 n shard_bytes bytes. */
+LCH_API int rs_encode(lch_ctx *ctx, uint32_t n, uint32_t k, int field, void *shards, size_t shard_bytes,
+                      void *stream);
+
+/* Erasure decoding (Sec. V, Algorithm 2, with the Appendix locator).
+ * shards holds the n rows of a received codeword.  erasure_mask is a HOST
+ * array of n bytes; a nonzero byte marks that row as erased.  Surviving rows
+ * are only read; each erased row j is overwritten with F(w_j).  With no
+ * erasures the call returns LCH_OK and does nothing; with more than n - k it
+ * returns LCH_ETOOMANY.  Rows that are not consistent with any codeword give
+ * a deterministic but meaningless result (erasure-only code).  Same n, k
+ * rules as rs_encode.  Uses context scratch of about 2 n shard_bytes bytes.
+ * The mask is copied before the call returns. */
+LCH_API int rs_decode(lch_ctx *ctx, uint32_t n, uint32_t k, int field, void *shards, size_t shard_bytes,
+                      const uint8_t *erasure_mask, void *stream);
+
+/* Static text for a status code. */
+LCH_API const char *lch_strerror(int status);
+
+/* Text of the last error raised on the calling host thread (never NULL). */
+LCH_API const char *lch_last_error(void);
+
+/* Number of kernels this context has launched so far (diagnostics). */
+LCH_API uint64_t lch_launch_count(const lch_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LCH_H */

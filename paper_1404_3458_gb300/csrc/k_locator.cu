@@ -1,0 +1,196 @@
+// K4: error-locator values (Appendix).
+//
+// Log Pi(j) = sum_y R(y) Log(w_j + w_y) over the n code points is a logical
+// (XOR) convolution of R (1 on erased rows) with L (L(y) = Log w_y, L(0) = 0),
+// computed as FWHT(FWHT(R) * FWHT(L)) modulo 2^r - 1 (eq. Rnmathrmw).  With n
+// points the two n-point FWHTs give n times the convolution, so the result is
+// scaled by n^-1 = 2^(r - lg n) mod 2^r - 1 (for n = 2^r this is 1, as in the
+// paper).  FWHT(L) depends only on (field, n) and is computed once.  The
+// exponent then gives Pi(j) for surviving j and Pi'(j) for erased j, the
+// denominators of Algorithm 2 step 6 (eqs. Pi(j), Pi'(j)).
+//
+// n <= 2^12 runs in one CTA in shared memory.  Larger n splits the index bits
+// into a low group (contiguous tiles) and a high group (strided tiles): the
+// two groups' Hadamard factors commute, so FWHT = FWHT_low o FWHT_high and the
+// pointwise product sits between the two high-group halves:
+//   pass A: FWHT_low(R)                      (contiguous tiles)
+//   pass B: FWHT_high, * FWHT(L), FWHT_high  (strided tiles)
+//   pass C: FWHT_low, scale, exponent        (contiguous tiles)
+// FWHT(L) itself is passes A and B on L.
+#include "lch_internal.cuh"
+
+namespace lch {
+
+namespace {
+
+__device__ __forceinline__ uint32_t madd(uint32_t a, uint32_t b, uint32_t M)
+{
+    uint32_t s = a + b;
+    return s >= M ? s - M : s;
+}
+__device__ __forceinline__ uint32_t msub(uint32_t a, uint32_t b, uint32_t M) { return a >= b ? a - b : a + M - b; }
+template <int R> __device__ __forceinline__ uint32_t mmul(uint32_t a, uint32_t b)
+{
+    constexpr uint32_t M = (1u << R) - 1;
+    uint64_t p = (uint64_t)a * b; // a, b < M, so p < 2^(2R)
+    p = (p & M) + (p >> R);
+    p = (p & M) + (p >> R);
+    return p >= M ? (uint32_t)(p - M) : (uint32_t)p;
+}
+
+__device__ __forceinline__ uint32_t mask_bit(const MaskBits &b, uint32_t j) { return (b.w[j >> 5] >> (j & 31u)) & 1u; }
+
+// In-place FWHT mod M of v[0 .. 2^lg) in shared memory.
+template <int R> __device__ void fwht_smem(uint32_t *v, uint32_t lg)
+{
+    constexpr uint32_t M = (1u << R) - 1;
+    const uint32_t half = (1u << lg) >> 1;
+    for (uint32_t lev = 0; lev < lg; lev++) {
+        for (uint32_t p = threadIdx.x; p < half; p += blockDim.x) {
+            uint32_t i = ((p >> lev) << (lev + 1)) | (p & ((1u << lev) - 1u));
+            uint32_t j = i + (1u << lev);
+            uint32_t x = v[i], y = v[j];
+            v[i] = madd(x, y, M);
+            v[j] = msub(x, y, M);
+        }
+        __syncthreads();
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void emit(uint32_t j, uint32_t c, uint32_t erased, const uint16_t *__restrict__ expt,
+                                     uint16_t *pre, uint16_t *post)
+{
+    constexpr uint32_t M = (1u << R) - 1;
+    pre[j] = erased ? 0 : expt[c];
+    post[j] = erased ? expt[c == 0 ? 0 : M - c] : 0;
+}
+
+// MODE 0: FWHT(L) -> fl_out.  MODE 1: full locator -> pre/post.
+template <int R, int MODE>
+__global__ void __launch_bounds__(1024) k_loc_small(uint32_t lgn, MaskBits bits, const uint16_t *__restrict__ logt,
+                                                    const uint16_t *__restrict__ expt, const uint32_t *__restrict__ fl,
+                                                    uint32_t *fl_out, uint16_t *pre, uint16_t *post, uint32_t ninv)
+{
+    extern __shared__ uint32_t v[];
+    const uint32_t n = 1u << lgn;
+    for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) v[j] = MODE == 0 ? (j ? logt[j] : 0u) : mask_bit(bits, j);
+    __syncthreads();
+    fwht_smem<R>(v, lgn);
+    if constexpr (MODE == 0) {
+        for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) fl_out[j] = v[j];
+    } else {
+        for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) v[j] = mmul<R>(v[j], fl[j]);
+        __syncthreads();
+        fwht_smem<R>(v, lgn);
+        for (uint32_t j = threadIdx.x; j < n; j += blockDim.x)
+            emit<R>(j, mmul<R>(v[j], ninv), mask_bit(bits, j), expt, pre, post);
+    }
+}
+
+// Pass A: contiguous tile of 2^a elements -> FWHT over the low bits.
+template <int R, int MODE>
+__global__ void __launch_bounds__(256) k_loc_a(uint32_t a, MaskBits bits, const uint16_t *__restrict__ logt,
+                                               uint32_t *work)
+{
+    extern __shared__ uint32_t v[];
+    const uint32_t base = blockIdx.x << a, len = 1u << a;
+    for (uint32_t u = threadIdx.x; u < len; u += blockDim.x) {
+        uint32_t j = base + u;
+        v[u] = MODE == 0 ? (j ? logt[j] : 0u) : mask_bit(bits, j);
+    }
+    __syncthreads();
+    fwht_smem<R>(v, a);
+    for (uint32_t u = threadIdx.x; u < len; u += blockDim.x) work[base + u] = v[u];
+}
+
+// Pass B: strided tile (fixed low bits) -> FWHT over the high bits
+// [, * FWHT(L), FWHT over the high bits].  Writes to `out` (the work array,
+// or the FWHT(L) table itself when MODE 0 finishes it here).
+template <int R, int MODE>
+__global__ void __launch_bounds__(256) k_loc_b(uint32_t a, uint32_t b, const uint32_t *__restrict__ fl,
+                                               const uint32_t *in, uint32_t *out)
+{
+    extern __shared__ uint32_t v[];
+    const uint32_t lo = blockIdx.x, len = 1u << b;
+    for (uint32_t u = threadIdx.x; u < len; u += blockDim.x) v[u] = in[(u << a) | lo];
+    __syncthreads();
+    fwht_smem<R>(v, b);
+    if (MODE == 1) {
+        for (uint32_t u = threadIdx.x; u < len; u += blockDim.x) v[u] = mmul<R>(v[u], fl[(u << a) | lo]);
+        __syncthreads();
+        fwht_smem<R>(v, b);
+    }
+    for (uint32_t u = threadIdx.x; u < len; u += blockDim.x) out[(u << a) | lo] = v[u];
+}
+
+// Pass C: contiguous tile -> FWHT over the low bits, scale, exponentiate,
+// emit pre/post.
+template <int R>
+__global__ void __launch_bounds__(256) k_loc_c(uint32_t a, MaskBits bits, const uint16_t *__restrict__ expt,
+                                               uint32_t ninv, const uint32_t *work, uint16_t *pre, uint16_t *post)
+{
+    extern __shared__ uint32_t v[];
+    const uint32_t base = blockIdx.x << a, len = 1u << a;
+    for (uint32_t u = threadIdx.x; u < len; u += blockDim.x) v[u] = work[base + u];
+    __syncthreads();
+    fwht_smem<R>(v, a);
+    for (uint32_t u = threadIdx.x; u < len; u += blockDim.x) {
+        uint32_t j = base + u;
+        emit<R>(j, mmul<R>(v[u], ninv), mask_bit(bits, j), expt, pre, post);
+    }
+}
+
+constexpr uint32_t kSmallLg = 12;
+
+template <int R>
+cudaError_t run(int mode, const FieldTables &t, uint32_t lgn, const MaskBits *bits, const uint32_t *fl,
+                uint32_t *fl_out, uint32_t *work, uint16_t *pre, uint16_t *post, cudaStream_t s, uint64_t *launches)
+{
+    constexpr uint32_t M = (1u << R) - 1;
+    const uint32_t ninv = (uint32_t)((1ull << (R - lgn)) % M);
+    static const MaskBits zero_bits = {};
+    const MaskBits &mb = bits ? *bits : zero_bits;
+    if (lgn <= kSmallLg) {
+        const uint32_t n = 1u << lgn;
+        const unsigned threads = n < 1024 ? (n < 32 ? 32 : n) : 1024;
+        const size_t smem = sizeof(uint32_t) * n;
+        if (mode == 0)
+            k_loc_small<R, 0><<<1, threads, smem, s>>>(lgn, mb, t.logt, t.expt, fl, fl_out, pre, post, ninv);
+        else
+            k_loc_small<R, 1><<<1, threads, smem, s>>>(lgn, mb, t.logt, t.expt, fl, fl_out, pre, post, ninv);
+        *launches += 1;
+        return cudaGetLastError();
+    }
+    const uint32_t a = (lgn + 1) / 2, b = lgn - a;
+    const size_t sa = sizeof(uint32_t) << a, sb = sizeof(uint32_t) << b;
+    if (mode == 0) { // FWHT(L) = FWHT_high(FWHT_low(L))
+        k_loc_a<R, 0><<<1u << b, 256, sa, s>>>(a, mb, t.logt, work);
+        k_loc_b<R, 0><<<1u << a, 256, sb, s>>>(a, b, fl, work, fl_out);
+        *launches += 2;
+        return cudaGetLastError();
+    }
+    k_loc_a<R, 1><<<1u << b, 256, sa, s>>>(a, mb, t.logt, work);
+    k_loc_b<R, 1><<<1u << a, 256, sb, s>>>(a, b, fl, work, work);
+    k_loc_c<R><<<1u << b, 256, sa, s>>>(a, mb, t.expt, ninv, work, pre, post);
+    *launches += 3;
+    return cudaGetLastError();
+}
+
+} // namespace
+
+cudaError_t launch_fwht_log_table(int r, const FieldTables &t, uint32_t lgn, uint32_t *fl, uint32_t *work,
+                                  cudaStream_t s, uint64_t *launches)
+{
+    if (r == 8) return run<8>(0, t, lgn, nullptr, nullptr, fl, work, nullptr, nullptr, s, launches);
+    return run<16>(0, t, lgn, nullptr, nullptr, fl, work, nullptr, nullptr, s, launches);
+}
+
+cudaError_t launch_locator(int r, const FieldTables &t, uint32_t lgn, const MaskBits &bits, const uint32_t *fl,
+                           uint32_t *work, uint16_t *pre, uint16_t *post, cudaStream_t s, uint64_t *launches)
+{
+    if (r == 8) return run<8>(1, t, lgn, &bits, fl, nullptr, work, pre, post, s, launches);
+    return run<16>(1, t, lgn, &bits, fl, nullptr, work, pre, post, s, launches);
+}
+
+} // namespace lch

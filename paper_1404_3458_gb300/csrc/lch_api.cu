@@ -1,0 +1,426 @@
+// C ABI (include/lch.h): argument checking, the per-device context with its
+// table cache and scratch, and the composition of the kernels into the
+// transform, derivative, encoder (Algorithm 1) and decoder (Algorithm 2).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/lch.h"
+#include "lch_internal.cuh"
+
+using namespace lch;
+
+struct lch_ctx {
+    int device = 0;
+    FieldTables tab[2];          // [0]: GF(2^8), [1]: GF(2^16)
+    uint32_t *fl[2][17] = {};    // FWHT of the log table per field and lg n
+    uint8_t *scratch = nullptr;  // grows on demand
+    size_t scratch_bytes = 0;
+    uint64_t launches = 0;
+};
+
+namespace {
+
+thread_local char g_err[512] = "no error";
+
+int fail(int status, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(LCH_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CU(call, what)                                                                             \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);                                        \
+    } while (0)
+
+// Makes the context's device current for the scope of one call.
+struct DeviceScope {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceScope(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceScope()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
+uint32_t lg2(uint64_t x)
+{
+    uint32_t l = 0;
+    while ((1ull << (l + 1)) <= x) l++;
+    return l;
+}
+
+int check_field(int field)
+{
+    if (field != LCH_GF8 && field != LCH_GF16) return fail(LCH_EINVAL, "field must be LCH_GF8 or LCH_GF16, got %d", field);
+    return LCH_OK;
+}
+
+int check_buffer(const void *buf, uint64_t rows, size_t shard_bytes)
+{
+    if (!buf) return fail(LCH_EINVAL, "buffer pointer is NULL");
+    if (((uintptr_t)buf) & 15u) return fail(LCH_EINVAL, "buffer pointer must be 16-byte aligned");
+    if (shard_bytes == 0 || (shard_bytes & 15u))
+        return fail(LCH_EINVAL, "shard_bytes must be a nonzero multiple of 16, got %zu", shard_bytes);
+    if (rows && shard_bytes > SIZE_MAX / rows) return fail(LCH_EINVAL, "rows * shard_bytes overflows");
+    return LCH_OK;
+}
+
+int check_len(const char *name, uint64_t h, int field)
+{
+    if (!is_pow2(h)) return fail(LCH_EINVAL, "%s must be a power of two, got %llu", name, (unsigned long long)h);
+    if (h > (1ull << field)) return fail(LCH_EINVAL, "%s must be at most 2^%d, got %llu", name, field, (unsigned long long)h);
+    return LCH_OK;
+}
+
+int ensure_tables(lch_ctx *ctx, int field, cudaStream_t s)
+{
+    FieldTables &t = ctx->tab[field == LCH_GF16];
+    if (t.ready) return LCH_OK;
+    cudaError_t e = build_field_tables(t, field, s, &ctx->launches);
+    if (e == cudaErrorMemoryAllocation) return fail(LCH_ENOMEM, "table allocation failed");
+    if (e != cudaSuccess) return cuda_fail(e, "building field tables");
+    return LCH_OK;
+}
+
+int ensure_scratch(lch_ctx *ctx, size_t bytes)
+{
+    if (bytes <= ctx->scratch_bytes) return LCH_OK;
+    // Work already queued may still use the old area.
+    CU(cudaDeviceSynchronize(), "synchronising before scratch growth");
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+    if (cudaMalloc(&ctx->scratch, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LCH_ENOMEM, "scratch allocation of %zu bytes failed", bytes);
+    }
+    ctx->scratch_bytes = bytes;
+    return LCH_OK;
+}
+
+int ensure_fl(lch_ctx *ctx, int field, uint32_t lgn, uint32_t *work, cudaStream_t s)
+{
+    uint32_t *&fl = ctx->fl[field == LCH_GF16][lgn];
+    if (fl) return LCH_OK;
+    if (cudaMalloc(&fl, sizeof(uint32_t) << lgn) != cudaSuccess) {
+        cudaGetLastError();
+        fl = nullptr;
+        return fail(LCH_ENOMEM, "allocation of the FWHT(log) table failed");
+    }
+    CU(launch_fwht_log_table(field, ctx->tab[field == LCH_GF16], lgn, fl, work, s, &ctx->launches),
+       "FWHT of the log table");
+    // Later calls may come on other streams: finish the table now.
+    CU(cudaStreamSynchronize(s), "synchronising the FWHT(log) table");
+    return LCH_OK;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Levels [0, lgh) are split into at most two passes of <= 8 levels each.
+void split_levels(uint32_t lgh, uint32_t *a, uint32_t *b)
+{
+    if (lgh <= 8) {
+        *a = lgh;
+        *b = 0;
+    } else {
+        *a = (lgh + 1) / 2;
+        *b = lgh - *a;
+    }
+}
+
+// h-point transform (inverse != 0: (Psi_h^l)^-1) from src to dst.
+int transform(lch_ctx *ctx, int field, uint32_t h, uint32_t l, int inverse, const uint8_t *src, uint8_t *dst,
+              size_t S, cudaStream_t s)
+{
+    const uint32_t lgh = lg2(h);
+    if (lgh == 0) {
+        if (src != dst) CU(cudaMemcpyAsync(dst, src, S, cudaMemcpyDeviceToDevice, s), "copy");
+        return LCH_OK;
+    }
+    uint32_t a, b;
+    split_levels(lgh, &a, &b);
+    PassArgs p;
+    p.S = S;
+    p.h = h;
+    p.l = l;
+    p.inverse = inverse;
+    p.rec = ctx->tab[field == LCH_GF16].rec;
+    // (Psi)^-1 runs the low levels first, Psi the high levels first.
+    uint32_t first_L0 = inverse ? 0 : a, first_n = inverse ? a : b;
+    uint32_t second_L0 = inverse ? a : 0, second_n = inverse ? b : a;
+    if (b == 0) {
+        first_L0 = 0;
+        first_n = a;
+    }
+    p.src = src;
+    p.dst = dst;
+    p.L0 = first_L0;
+    p.nlev = first_n;
+    CU(launch_pass(field, p, s, &ctx->launches), "transform pass");
+    if (b) {
+        p.src = dst;
+        p.L0 = second_L0;
+        p.nlev = second_n;
+        CU(launch_pass(field, p, s, &ctx->launches), "transform pass");
+    }
+    return LCH_OK;
+}
+
+// dst = [src]' (coefficient vectors of h rows); src is scaled in place.
+int derivative(lch_ctx *ctx, int field, uint32_t h, uint8_t *src, uint8_t *dst, size_t S, cudaStream_t s)
+{
+    const FieldTables &t = ctx->tab[field == LCH_GF16];
+    const uint32_t lgh = lg2(h);
+    if (lgh == 0) {
+        CU(cudaMemsetAsync(dst, 0, S, s), "memset");
+        return LCH_OK;
+    }
+    // d^d_i = d_i B_i (eq. dimathrmd)
+    CU(launch_rowscale(field, src, src, S, h, t.B, 0, s, &ctx->launches), "derivative scale");
+    uint32_t a, b;
+    split_levels(lgh, &a, &b);
+    SupersetArgs q;
+    q.src = src;
+    q.dst = dst;
+    q.S = S;
+    q.h = h;
+    q.L0 = 0;
+    q.nlev = a;
+    q.accumulate = 0;
+    CU(launch_superset(q, s, &ctx->launches), "derivative sums");
+    if (b) {
+        q.L0 = a;
+        q.nlev = b;
+        q.accumulate = 1;
+        CU(launch_superset(q, s, &ctx->launches), "derivative sums");
+    }
+    // divide coefficient j by B_j (eq. XDhx3)
+    CU(launch_rowscale(field, dst, dst, S, h, t.Binv, 0, s, &ctx->launches), "derivative scale");
+    return LCH_OK;
+}
+
+int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards, size_t S, const uint8_t *mask,
+                cudaStream_t s)
+{
+    const uint32_t lgn = lg2(n);
+    MaskBits bits;
+    memset(&bits, 0, sizeof(bits));
+    uint32_t ne = 0;
+    for (uint32_t j = 0; j < n; j++)
+        if (mask[j]) {
+            bits.w[j >> 5] |= 1u << (j & 31);
+            ne++;
+        }
+    if (ne == 0) return LCH_OK;
+    if (ne > n - k) return fail(LCH_ETOOMANY, "%u erasures exceed n - k = %u", ne, n - k);
+    int rc = ensure_tables(ctx, field, s);
+    if (rc) return rc;
+    const size_t body = (size_t)n * S;
+    const size_t off_phi2 = align_up(body), off_pre = off_phi2 + align_up(body);
+    const size_t off_post = off_pre + align_up(sizeof(uint16_t) * n);
+    const size_t off_work = off_post + align_up(sizeof(uint16_t) * n);
+    rc = ensure_scratch(ctx, off_work + align_up(sizeof(uint32_t) * n));
+    if (rc) return rc;
+    uint8_t *phi = ctx->scratch, *phi2 = ctx->scratch + off_phi2;
+    uint16_t *pre = reinterpret_cast<uint16_t *>(ctx->scratch + off_pre);
+    uint16_t *post = reinterpret_cast<uint16_t *>(ctx->scratch + off_post);
+    uint32_t *work = reinterpret_cast<uint32_t *>(ctx->scratch + off_work);
+    rc = ensure_fl(ctx, field, lgn, work, s);
+    if (rc) return rc;
+    const FieldTables &t = ctx->tab[field == LCH_GF16];
+    // Step 1: Pi(j) off E and 1/Pi'(j) on E.
+    CU(launch_locator(field, t, lgn, bits, ctx->fl[field == LCH_GF16][lgn], work, pre, post, s, &ctx->launches),
+       "locator");
+    // Step 2: Phi = F * Pi, zero on erased rows (eq. hatF(l)).
+    CU(launch_rowscale(field, phi, shards, S, n, pre, 0, s, &ctx->launches), "Phi");
+    // Step 3: coefficients of hatF.
+    rc = transform(ctx, field, n, 0, 1, phi, phi, S, s);
+    if (rc) return rc;
+    // Step 4: formal derivative.
+    rc = derivative(ctx, field, n, phi, phi2, S, s);
+    if (rc) return rc;
+    // Step 5: evaluate hatF'.
+    rc = transform(ctx, field, n, 0, 0, phi2, phi2, S, s);
+    if (rc) return rc;
+    // Step 6: F(j) = hatF'(j) / Pi'(j), written to the erased rows only.
+    CU(launch_rowscale(field, shards, phi2, S, n, post, 1, s, &ctx->launches), "erasures");
+    return LCH_OK;
+}
+
+int encode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards, size_t S, cudaStream_t s)
+{
+    if (k == n) return LCH_OK;
+    if (!is_pow2(k)) {
+        // Shortened code: recover rows k..n-1 as erasures (same unique F).
+        uint8_t *mask = new uint8_t[n];
+        memset(mask, 0, k);
+        memset(mask + k, 1, n - k);
+        int rc = decode_impl(ctx, n, k, field, shards, S, mask, s);
+        delete[] mask;
+        return rc;
+    }
+    int rc = ensure_tables(ctx, field, s);
+    if (rc) return rc;
+    rc = ensure_scratch(ctx, (size_t)k * S);
+    if (rc) return rc;
+    uint8_t *mbar = ctx->scratch;
+    // Algorithm 1 line 1: bar M_k = (Psi_k^0)^-1 [M_k]
+    rc = transform(ctx, field, k, 0, 1, shards, mbar, S, s);
+    if (rc) return rc;
+    // lines 2-4: bar F_i = Psi_k^{ik} [bar M_k] into rows ik .. ik+k-1
+    for (uint32_t i = 1; i < n / k; i++) {
+        rc = transform(ctx, field, k, i * k, 0, mbar, shards + (size_t)i * k * S, S, s);
+        if (rc) return rc;
+    }
+    return LCH_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+LCH_API int lch_ctx_create(lch_ctx **out, int device)
+{
+    if (!out) return fail(LCH_EINVAL, "ctx output pointer is NULL");
+    *out = nullptr;
+    int count = 0;
+    CU(cudaGetDeviceCount(&count), "cudaGetDeviceCount");
+    if (device < 0 || device >= count) return fail(LCH_EINVAL, "device %d out of range (have %d)", device, count);
+    {
+        DeviceScope ds(device);
+        if (!ds.ok) return fail(LCH_ECUDA, "cannot select device %d", device);
+        CU(configure_transform_kernels(), "configuring kernels");
+    }
+    lch_ctx *ctx = new (std::nothrow) lch_ctx;
+    if (!ctx) return fail(LCH_ENOMEM, "host allocation failed");
+    ctx->device = device;
+    *out = ctx;
+    return LCH_OK;
+}
+
+LCH_API void lch_ctx_destroy(lch_ctx *ctx)
+{
+    if (!ctx) return;
+    {
+        DeviceScope ds(ctx->device);
+        cudaDeviceSynchronize();
+        for (auto &t : ctx->tab) {
+            cudaFree(t.fval);
+            cudaFree(t.rec);
+            cudaFree(t.B);
+            cudaFree(t.Binv);
+            cudaFree(t.expt);
+            cudaFree(t.logt);
+        }
+        for (auto &row : ctx->fl)
+            for (auto *p : row) cudaFree(p);
+        cudaFree(ctx->scratch);
+    }
+    delete ctx;
+}
+
+LCH_API int lch_fft(lch_ctx *ctx, int field, uint32_t h, uint32_t l, void *buf, size_t shard_bytes, void *stream)
+{
+    int rc;
+    if ((rc = check_field(field)) || (rc = check_len("h", h, field)) || (rc = check_buffer(buf, h, shard_bytes))) return rc;
+    if (l >= (1u << field)) return fail(LCH_EINVAL, "shift l must be below 2^%d, got %u", field, l);
+    if (!ctx) return fail(LCH_EINVAL, "ctx is NULL");
+    DeviceScope ds(ctx->device);
+    if (!ds.ok) return fail(LCH_ECUDA, "cannot select device %d", ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ensure_tables(ctx, field, s))) return rc;
+    uint8_t *p = (uint8_t *)buf;
+    return transform(ctx, field, h, l, 0, p, p, shard_bytes, s);
+}
+
+LCH_API int lch_ifft(lch_ctx *ctx, int field, uint32_t h, uint32_t l, void *buf, size_t shard_bytes, void *stream)
+{
+    int rc;
+    if ((rc = check_field(field)) || (rc = check_len("h", h, field)) || (rc = check_buffer(buf, h, shard_bytes))) return rc;
+    if (l >= (1u << field)) return fail(LCH_EINVAL, "shift l must be below 2^%d, got %u", field, l);
+    if (!ctx) return fail(LCH_EINVAL, "ctx is NULL");
+    DeviceScope ds(ctx->device);
+    if (!ds.ok) return fail(LCH_ECUDA, "cannot select device %d", ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ensure_tables(ctx, field, s))) return rc;
+    uint8_t *p = (uint8_t *)buf;
+    return transform(ctx, field, h, l, 1, p, p, shard_bytes, s);
+}
+
+LCH_API int lch_derivative(lch_ctx *ctx, int field, uint32_t h, void *buf, size_t shard_bytes, void *stream)
+{
+    int rc;
+    if ((rc = check_field(field)) || (rc = check_len("h", h, field)) || (rc = check_buffer(buf, h, shard_bytes))) return rc;
+    if (!ctx) return fail(LCH_EINVAL, "ctx is NULL");
+    DeviceScope ds(ctx->device);
+    if (!ds.ok) return fail(LCH_ECUDA, "cannot select device %d", ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ensure_tables(ctx, field, s))) return rc;
+    if ((rc = ensure_scratch(ctx, (size_t)h * shard_bytes))) return rc;
+    uint8_t *p = (uint8_t *)buf;
+    if ((rc = derivative(ctx, field, h, p, ctx->scratch, shard_bytes, s))) return rc;
+    CU(cudaMemcpyAsync(p, ctx->scratch, (size_t)h * shard_bytes, cudaMemcpyDeviceToDevice, s), "copy back");
+    return LCH_OK;
+}
+
+LCH_API int rs_encode(lch_ctx *ctx, uint32_t n, uint32_t k, int field, void *shards, size_t shard_bytes, void *stream)
+{
+    int rc;
+    if ((rc = check_field(field)) || (rc = check_len("n", n, field)) || (rc = check_buffer(shards, n, shard_bytes)))
+        return rc;
+    if (k == 0 || k > n) return fail(LCH_EINVAL, "k must satisfy 1 <= k <= n, got k=%u n=%u", k, n);
+    if (!ctx) return fail(LCH_EINVAL, "ctx is NULL");
+    DeviceScope ds(ctx->device);
+    if (!ds.ok) return fail(LCH_ECUDA, "cannot select device %d", ctx->device);
+    return encode_impl(ctx, n, k, field, (uint8_t *)shards, shard_bytes, (cudaStream_t)stream);
+}
+
+LCH_API int rs_decode(lch_ctx *ctx, uint32_t n, uint32_t k, int field, void *shards, size_t shard_bytes,
+                      const uint8_t *erasure_mask, void *stream)
+{
+    int rc;
+    if ((rc = check_field(field)) || (rc = check_len("n", n, field)) || (rc = check_buffer(shards, n, shard_bytes)))
+        return rc;
+    if (k == 0 || k > n) return fail(LCH_EINVAL, "k must satisfy 1 <= k <= n, got k=%u n=%u", k, n);
+    if (!erasure_mask) return fail(LCH_EINVAL, "erasure_mask is NULL");
+    if (!ctx) return fail(LCH_EINVAL, "ctx is NULL");
+    DeviceScope ds(ctx->device);
+    if (!ds.ok) return fail(LCH_ECUDA, "cannot select device %d", ctx->device);
+    return decode_impl(ctx, n, k, field, (uint8_t *)shards, shard_bytes, erasure_mask, (cudaStream_t)stream);
+}
+
+LCH_API const char *lch_strerror(int status)
+{
+    switch (status) {
+    case LCH_OK: return "success";
+    case LCH_EINVAL: return "invalid argument";
+    case LCH_ETOOMANY: return "more erasures than n - k";
+    case LCH_ENOMEM: return "out of memory";
+    case LCH_ECUDA: return "CUDA error";
+    default: return "unknown status";
+    }
+}
+
+LCH_API const char *lch_last_error(void) { return g_err; }
+
+LCH_API uint64_t lch_launch_count(const lch_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+} // extern "C"

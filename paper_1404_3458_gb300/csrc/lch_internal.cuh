@@ -1,0 +1,175 @@
+// Internal declarations shared by the CUDA translation units of liblch.
+//
+// Field model (Sec. II.A): GF(2^r), r in {8, 16}; the point w_i is the element
+// whose bit pattern is i (basis v_j = x^j).  Elements are packed in 32-bit
+// words: four bytes for GF(2^8), two little-endian halves for GF(2^16).
+//
+// Multiplication by a constant c uses a "split table" record built once per
+// constant: GF(2^8) keeps the 256 products c*e; GF(2^16) keeps c*e, c*(e<<6)
+// (e < 64) and c*(e<<12) (e < 16), so c*a is three lookups XORed together.
+// A 64-entry uint16 table spans 32 consecutive 32-bit words, i.e. all 32
+// shared-memory banks once each, so a warp's lookups never conflict.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lch {
+
+template <int R> struct FT;
+template <> struct FT<8> {
+    static constexpr uint32_t poly = 0x11Du;   // x^8 + x^4 + x^3 + x^2 + 1
+    static constexpr uint32_t rec_bytes = 256; // one 256-entry byte table
+    static constexpr uint32_t rec_entries = 256;
+};
+template <> struct FT<16> {
+    static constexpr uint32_t poly = 0x1100Bu; // x^16 + x^12 + x^3 + x + 1
+    static constexpr uint32_t rec_bytes = 288; // 64 + 64 + 16 uint16 entries
+    static constexpr uint32_t rec_entries = 144;
+};
+
+// Shift-and-add product with reduction after every doubling ("xtime").
+template <int R>
+__host__ __device__ __forceinline__ uint32_t gf_mul_slow(uint32_t a, uint32_t b)
+{
+    uint32_t p = 0;
+#pragma unroll
+    for (int i = 0; i < R; i++) {
+        if (b & 1u) p ^= a;
+        b >>= 1;
+        a <<= 1;
+        if (a >> R) a ^= FT<R>::poly;
+    }
+    return p;
+}
+
+// a^(2^R - 2) = a^-1 for a != 0 (and 0 for a == 0).
+template <int R>
+__host__ __device__ inline uint32_t gf_inv_slow(uint32_t a)
+{
+    uint32_t acc = 1, base = a;
+    uint32_t e = (1u << R) - 2;
+    while (e) {
+        if (e & 1u) acc = gf_mul_slow<R>(acc, base);
+        base = gf_mul_slow<R>(base, base);
+        e >>= 1;
+    }
+    return acc;
+}
+
+// Entry `idx` of the split-table record of constant c.
+template <int R> __device__ __forceinline__ uint32_t rec_entry(uint32_t c, uint32_t idx);
+template <> __device__ __forceinline__ uint32_t rec_entry<8>(uint32_t c, uint32_t idx)
+{
+    return gf_mul_slow<8>(c, idx);
+}
+template <> __device__ __forceinline__ uint32_t rec_entry<16>(uint32_t c, uint32_t idx)
+{
+    uint32_t sub = idx < 64 ? 0 : (idx < 128 ? 1 : 2);
+    uint32_t e = idx - sub * 64;
+    return gf_mul_slow<16>(c, e << (6 * sub));
+}
+
+template <int R> __device__ __forceinline__ void rec_store(uint8_t *rec, uint32_t idx, uint32_t v);
+template <> __device__ __forceinline__ void rec_store<8>(uint8_t *rec, uint32_t idx, uint32_t v)
+{
+    rec[idx] = (uint8_t)v;
+}
+template <> __device__ __forceinline__ void rec_store<16>(uint8_t *rec, uint32_t idx, uint32_t v)
+{
+    reinterpret_cast<uint16_t *>(rec)[idx] = (uint16_t)v;
+}
+
+// Multiply every element packed in word w by the constant whose record is T.
+template <int R> __device__ __forceinline__ uint32_t mul_word(uint32_t w, const uint8_t *T);
+template <> __device__ __forceinline__ uint32_t mul_word<8>(uint32_t w, const uint8_t *T)
+{
+    return (uint32_t)T[w & 255u] | ((uint32_t)T[(w >> 8) & 255u] << 8) |
+           ((uint32_t)T[(w >> 16) & 255u] << 16) | ((uint32_t)T[w >> 24] << 24);
+}
+template <> __device__ __forceinline__ uint32_t mul_word<16>(uint32_t w, const uint8_t *Tb)
+{
+    const uint16_t *T = reinterpret_cast<const uint16_t *>(Tb);
+    uint32_t lo = (uint32_t)T[w & 63u] ^ (uint32_t)T[64 + ((w >> 6) & 63u)] ^ (uint32_t)T[128 + ((w >> 12) & 15u)];
+    uint32_t hi = (uint32_t)T[(w >> 16) & 63u] ^ (uint32_t)T[64 + ((w >> 22) & 63u)] ^ (uint32_t)T[128 + (w >> 28)];
+    return lo | (hi << 16);
+}
+
+// Offset of level i in the per-level factor arrays: level i holds 2^(r-i)
+// entries, one per value of (x >> i), x in [0, 2^r).
+__host__ __device__ __forceinline__ uint32_t level_off(int r, int i)
+{
+    return (1u << (r + 1)) - (1u << (r + 1 - i));
+}
+__host__ __device__ __forceinline__ uint32_t factor_count(int r) { return (1u << (r + 1)) - 1; }
+
+// Device-resident tables of one field, built by the precompute kernels.
+struct FieldTables {
+    int r = 0;
+    bool ready = false;
+    uint16_t *fval = nullptr; // hatW_i(w_{y 2^i}) at level_off(r,i) + y
+    uint8_t *rec = nullptr;   // split-table record of each fval entry
+    uint16_t *B = nullptr;    // B_j = prod_{m in I_j} W'_m, j < 2^r   (eq. B)
+    uint16_t *Binv = nullptr; // B_j^-1
+    uint16_t *expt = nullptr; // alpha^i, i < 2^r - 1
+    uint16_t *logt = nullptr; // log_alpha(x), x != 0; logt[0] = 0
+    uint32_t wbase[16] = {};  // W_i(w_{2^i}) (host copy, for tests/diagnostics)
+};
+
+// ----------------------------------------------------------------- launches
+// Every launcher returns the CUDA error of its launch and adds the number of
+// kernels it launched to *launches.
+
+cudaError_t build_field_tables(FieldTables &t, int r, cudaStream_t s, uint64_t *launches);
+
+// Opt the large-shared-memory kernels in on the current device.
+cudaError_t configure_transform_kernels();
+
+// One transform pass: levels [L0, L0 + nlev) of an h-row transform, applied
+// to tiles of 2^nlev rows (row stride 2^L0) that are read from src and written
+// to dst (src == dst allowed).
+struct PassArgs {
+    const uint8_t *src;
+    uint8_t *dst;
+    size_t S;         // shard bytes
+    uint32_t h;       // transform length
+    uint32_t L0;      // first level of the pass
+    uint32_t nlev;    // levels in the pass, 1..8
+    uint32_t l;       // shift
+    int inverse;      // 1: (Psi)^-1 order, 0: Psi order
+    const uint8_t *rec;
+};
+cudaError_t launch_pass(int r, const PassArgs &a, cudaStream_t s, uint64_t *launches);
+
+// Derivative helper: dst[t] (^)= XOR over l in [L0, L0+nlev) with bit l of t
+// clear of src[t + 2^l]   (one bit range of eq. XDhx3's inner sum).
+struct SupersetArgs {
+    const uint8_t *src;
+    uint8_t *dst;
+    size_t S;
+    uint32_t h;
+    uint32_t L0;
+    uint32_t nlev;
+    int accumulate;
+};
+cudaError_t launch_superset(const SupersetArgs &a, cudaStream_t s, uint64_t *launches);
+
+// dst[t] = src[t] * coef[t] for t < rows (a zero coefficient zeroes the row);
+// with skip_zero, rows whose coefficient is zero are left untouched.
+cudaError_t launch_rowscale(int r, uint8_t *dst, const uint8_t *src, size_t S, uint32_t rows,
+                            const uint16_t *coef, int skip_zero, cudaStream_t s, uint64_t *launches);
+
+// Error locator (Appendix): from the erasure bitmap, pre[j] = Pi(w_j) for
+// surviving j and 0 for erased j; post[j] = 1/Pi'(w_j) for erased j, 0 else.
+constexpr uint32_t kMaxN = 65536;
+struct MaskBits {
+    uint32_t w[kMaxN / 32];
+};
+cudaError_t launch_fwht_log_table(int r, const FieldTables &t, uint32_t lgn, uint32_t *fl,
+                                  uint32_t *work, cudaStream_t s, uint64_t *launches);
+cudaError_t launch_locator(int r, const FieldTables &t, uint32_t lgn, const MaskBits &bits,
+                           const uint32_t *fl, uint32_t *work, uint16_t *pre, uint16_t *post,
+                           cudaStream_t s, uint64_t *launches);
+
+} // namespace lch

@@ -1,0 +1,149 @@
+"""Thin Python binding of the liblch C ABI (``include/lch.h``).
+
+Argument marshalling only: every step of every call runs in the CUDA kernels
+of ``liblch.so``.  Data arguments are CUDA ``torch.uint8`` tensors of shape
+``[rows, shard_bytes]`` (contiguous, 16-byte aligned); calls are enqueued on
+torch's current CUDA stream unless a stream is given.  The library is loaded
+from this package directory; if it is missing or fails to load, every call
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblch.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "lch.h")
+
+LCH_OK, LCH_EINVAL, LCH_ETOOMANY, LCH_ENOMEM, LCH_ECUDA = 0, 1, 2, 3, 4
+GF8, GF16 = 8, 16
+
+_lib = None
+
+
+class LchError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+def declared_functions():
+    """Names of the entry points that include/lch.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    return re.findall(r"LCH_API\s+[\w\s\*]+?\b(\w+)\s*\(", text)
+
+
+def load() -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"liblch.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, u32, sz, i = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_size_t, ctypes.c_int
+    sigs = {
+        "lch_ctx_create": (i, [ctypes.POINTER(vp), i]),
+        "lch_ctx_destroy": (None, [vp]),
+        "lch_fft": (i, [vp, i, u32, u32, vp, sz, vp]),
+        "lch_ifft": (i, [vp, i, u32, u32, vp, sz, vp]),
+        "lch_derivative": (i, [vp, i, u32, vp, sz, vp]),
+        "rs_encode": (i, [vp, u32, u32, i, vp, sz, vp]),
+        "rs_decode": (i, [vp, u32, u32, i, vp, sz, vp, vp]),
+        "lch_strerror": (ctypes.c_char_p, [i]),
+        "lch_last_error": (ctypes.c_char_p, []),
+        "lch_launch_count": (ctypes.c_uint64, [vp]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    return load().lch_last_error().decode()
+
+
+def _check(status: int):
+    if status != LCH_OK:
+        raise LchError(status, last_error())
+
+
+def _stream_handle(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _buf(t, rows=None):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.uint8:
+        raise TypeError("expected a CUDA uint8 tensor of shape [rows, shard_bytes]")
+    if t.dim() != 2 or not t.is_contiguous():
+        raise ValueError("expected a contiguous 2-D tensor [rows, shard_bytes]")
+    if rows is not None and t.shape[0] != rows:
+        raise ValueError(f"expected {rows} rows, got {t.shape[0]}")
+    return ctypes.c_void_p(t.data_ptr()), t.shape[1]
+
+
+class Context:
+    """A liblch context on one CUDA device (owns tables and scratch)."""
+
+    def __init__(self, device: int = 0):
+        L = load()
+        h = ctypes.c_void_p()
+        _check(L.lch_ctx_create(ctypes.byref(h), int(device)))
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lch_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def launches(self) -> int:
+        return int(load().lch_launch_count(self._h))
+
+    # Sec. III: Psi_h^l and its inverse, in place on h rows.
+    def fft(self, field: int, l: int, buf, stream=None):
+        p, S = _buf(buf)
+        _check(load().lch_fft(self._h, field, buf.shape[0], l, p, S, _stream_handle(stream)))
+
+    def ifft(self, field: int, l: int, buf, stream=None):
+        p, S = _buf(buf)
+        _check(load().lch_ifft(self._h, field, buf.shape[0], l, p, S, _stream_handle(stream)))
+
+    # Sec. IV: formal derivative, in place on h rows.
+    def derivative(self, field: int, buf, stream=None):
+        p, S = _buf(buf)
+        _check(load().lch_derivative(self._h, field, buf.shape[0], p, S, _stream_handle(stream)))
+
+    # Sec. V, Algorithm 1.
+    def rs_encode(self, n: int, k: int, field: int, shards, stream=None):
+        p, S = _buf(shards, n)
+        _check(load().rs_encode(self._h, n, k, field, p, S, _stream_handle(stream)))
+
+    # Sec. V, Algorithm 2.  erasure_mask: n bytes on the host, nonzero = erased.
+    def rs_decode(self, n: int, k: int, field: int, shards, erasure_mask, stream=None):
+        p, S = _buf(shards, n)
+        m = np.ascontiguousarray(np.asarray(erasure_mask, dtype=np.uint8).reshape(-1))
+        if m.size != n:
+            raise ValueError(f"erasure mask must have n={n} entries")
+        _check(load().rs_decode(self._h, n, k, field, p, S, m.ctypes.data_as(ctypes.c_void_p),
+                                _stream_handle(stream)))

@@ -1,0 +1,71 @@
+"""The C ABI loads, exports every entry point include/lch.h declares, and
+rejects bad arguments on the host before touching a GPU (no compute calls)."""
+import ctypes
+
+import pytest
+
+from paper_1404_3458_gb300 import build as B
+from paper_1404_3458_gb300 import lch
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return lch.load()
+
+
+def test_exports_every_declared_symbol(L):
+    names = lch.declared_functions()
+    assert set(names) >= {"lch_ctx_create", "lch_ctx_destroy", "lch_fft", "lch_ifft", "lch_derivative",
+                          "rs_encode", "rs_decode", "lch_strerror", "lch_last_error", "lch_launch_count"}
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_strerror(L):
+    assert L.lch_strerror(0) == b"success"
+    assert L.lch_strerror(lch.LCH_ETOOMANY) == b"more erasures than n - k"
+    assert L.lch_strerror(99) == b"unknown status"
+
+
+FAKE = ctypes.c_void_p(0x10000)       # 16-byte aligned, never dereferenced
+MISALIGNED = ctypes.c_void_p(0x10008)
+
+
+@pytest.mark.parametrize("args,needle", [
+    ((None, 33, 16, 8, FAKE, 1024, None), "n must be a power of two"),
+    ((None, 512, 16, 8, FAKE, 1024, None), "at most 2^8"),
+    ((None, 32, 0, 8, FAKE, 1024, None), "1 <= k <= n"),
+    ((None, 32, 33, 8, FAKE, 1024, None), "1 <= k <= n"),
+    ((None, 32, 16, 12, FAKE, 1024, None), "field must be"),
+    ((None, 32, 16, 8, FAKE, 1000, None), "multiple of 16"),
+    ((None, 32, 16, 8, FAKE, 0, None), "multiple of 16"),
+    ((None, 32, 16, 8, MISALIGNED, 1024, None), "16-byte aligned"),
+    ((None, 32, 16, 8, None, 1024, None), "NULL"),
+    ((None, 32, 16, 8, FAKE, 1024, None), "ctx is NULL"),
+])
+def test_encode_argument_checks(L, args, needle):
+    assert L.rs_encode(*args) == lch.LCH_EINVAL
+    assert needle in lch.last_error()
+
+
+def test_decode_and_transform_argument_checks(L):
+    mask = (ctypes.c_uint8 * 32)()
+    assert L.rs_decode(None, 32, 16, 8, FAKE, 1024, None, None) == lch.LCH_EINVAL
+    assert "erasure_mask is NULL" in lch.last_error()
+    assert L.rs_decode(None, 65536 * 2, 16, 16, FAKE, 1024, mask, None) == lch.LCH_EINVAL
+    assert L.lch_fft(None, 16, 256, 65536, FAKE, 64, None) == lch.LCH_EINVAL
+    assert "shift l" in lch.last_error()
+    assert L.lch_ifft(None, 8, 3, 0, FAKE, 64, None) == lch.LCH_EINVAL
+    assert L.lch_derivative(None, 16, 1 << 17, FAKE, 64, None) == lch.LCH_EINVAL
+    assert L.lch_fft(None, 16, 256, 0, FAKE, 64, None) == lch.LCH_EINVAL
+    assert "ctx is NULL" in lch.last_error()
+    assert L.lch_launch_count(None) == 0
+    L.lch_ctx_destroy(None)  # ignored
+
+
+def test_python_binding_refuses_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(lch, "_lib", None)
+    monkeypatch.setattr(lch, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        lch.load()

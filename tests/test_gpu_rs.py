@@ -1,0 +1,139 @@
+"""GPU parity: rs_encode / rs_decode against the CPU oracle, bit-exact, on
+the measured workloads (small_gf8, medium_gf16, large_gf16) and edge cases."""
+import itertools
+
+import numpy as np
+import pytest
+
+from helpers import elem_cols, elems, to_dev
+from oracle import oracle as O
+from paper_1404_3458_gb300 import lch
+from paper_1404_3458_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+def message(n, k, S, seed):
+    host = np.zeros((n, S), dtype=np.uint8)
+    host[:k] = WL.shards(k, S, seed)
+    return host
+
+
+def gpu_encode(ctx, r, n, k, host):
+    dev = to_dev(host)
+    ctx.rs_encode(n, k, r, dev)
+    return dev.cpu().numpy()
+
+
+def gpu_decode(ctx, r, n, k, cw, mask, fill=0x5A):
+    bad = cw.copy()
+    bad[mask != 0] = fill
+    dev = to_dev(bad)
+    ctx.rs_decode(n, k, r, dev, mask)
+    return dev.cpu().numpy()
+
+
+@pytest.mark.parametrize("r,n,k,S", [(8, 32, 16, 1024), (8, 8, 4, 16), (8, 256, 128, 48), (8, 64, 16, 4112),
+                                     (16, 64, 32, 2064), (16, 256, 64, 208), (8, 16, 1, 32), (16, 16, 16, 16),
+                                     (8, 64, 48, 80), (16, 128, 96, 64), (8, 32, 3, 16), (16, 512, 500, 32)])
+def test_encode_matches_oracle(ctx, r, n, k, S):
+    host = message(n, k, S, seed=n + k + S)
+    got = gpu_encode(ctx, r, n, k, host)
+    cols = elem_cols(S, r, 32, seed=n)
+    expect = O.rs_encode(r, n, k, elems(host, r, cols))
+    assert np.array_equal(elems(got, r)[:, cols], expect)
+    assert np.array_equal(got[:k], host[:k])
+
+
+def test_small_gf8_workload_full(ctx):
+    w = WL.WORKLOADS["small_gf8"]
+    host = message(w.n, w.k, w.shard_bytes, w.seed)
+    cw = gpu_encode(ctx, w.field, w.n, w.k, host)
+    expect = O.from_elems(O.rs_encode(w.field, w.n, w.k, elems(host, w.field)), w.field)
+    assert np.array_equal(cw, expect)
+    mask = WL.erasure_mask(w.n, w.erasures, w.seed)
+    assert np.array_equal(gpu_decode(ctx, w.field, w.n, w.k, cw, mask), cw)
+    # the oracle recovers the same rows from the same survivors
+    bad = cw.copy()
+    bad[mask == 1] = 0
+    ref = O.from_elems(O.rs_decode(w.field, w.n, w.k, elems(bad, w.field), mask), w.field)
+    assert np.array_equal(ref, cw)
+
+
+def test_exhaustive_8_4_all_patterns(ctx):
+    """Every pattern of at most 4 erasures on (8,4) over GF(2^8): 163 decodes."""
+    r, n, k, S = 8, 8, 4, 32
+    cw = gpu_encode(ctx, r, n, k, message(n, k, S, seed=84))
+    count = 0
+    for e in range(n - k + 1):
+        for erased in itertools.combinations(range(n), e):
+            mask = np.zeros(n, dtype=np.uint8)
+            mask[list(erased)] = 1
+            assert np.array_equal(gpu_decode(ctx, r, n, k, cw, mask), cw), erased
+            count += 1
+    assert count == 163
+
+
+@pytest.mark.parametrize("r,n,k,S,e", [(8, 32, 16, 1024, 16), (8, 32, 16, 1024, 5), (8, 256, 128, 48, 128),
+                                       (16, 64, 32, 2064, 32), (16, 1024, 512, 32, 512), (16, 8192, 4096, 16, 4000),
+                                       (8, 64, 48, 80, 16), (16, 128, 96, 64, 1), (16, 4096, 2048, 48, 2048)])
+def test_decode_matches_oracle(ctx, r, n, k, S, e):
+    host = message(n, k, S, seed=5 * n + e)
+    cw = gpu_encode(ctx, r, n, k, host)
+    mask = WL.erasure_mask(n, e, seed=n * 3 + e)
+    got = gpu_decode(ctx, r, n, k, cw, mask)
+    assert np.array_equal(got, cw)
+    cols = elem_cols(S, r, 4, seed=e)
+    bad = elems(cw, r, cols)
+    bad[mask == 1] = 0
+    rows = np.nonzero(mask)[0][:64]
+    ref = O.rs_decode(r, n, k, bad, mask, rows=rows)
+    assert np.array_equal(elems(got, r, cols)[rows], ref[rows])
+
+
+def test_decode_edge_cases(ctx):
+    r, n, k, S = 16, 64, 32, 64
+    cw = gpu_encode(ctx, r, n, k, message(n, k, S, seed=9))
+    # zero erasures: a no-op, even on corrupted data
+    dev = to_dev(cw)
+    ctx.rs_decode(n, k, r, dev, np.zeros(n, np.uint8))
+    assert np.array_equal(dev.cpu().numpy(), cw)
+    # more than n - k erasures: refused, buffer untouched
+    mask = np.zeros(n, np.uint8)
+    mask[: n - k + 1] = 1
+    dev = to_dev(cw)
+    with pytest.raises(lch.LchError) as ei:
+        ctx.rs_decode(n, k, r, dev, mask)
+    assert ei.value.status == lch.LCH_ETOOMANY
+    assert np.array_equal(dev.cpu().numpy(), cw)
+    # all message rows erased, and all parity rows erased
+    for mask in (WL.burst_mask(n, n - k, 0), WL.burst_mask(n, n - k, k)):
+        assert np.array_equal(gpu_decode(ctx, r, n, k, cw, mask), cw)
+
+
+def test_medium_gf16_workload(ctx):
+    w = WL.WORKLOADS["medium_gf16"]
+    host = message(w.n, w.k, w.shard_bytes, w.seed)
+    cw = gpu_encode(ctx, w.field, w.n, w.k, host)
+    cols = elem_cols(w.shard_bytes, w.field, 48, seed=2)
+    assert np.array_equal(elems(cw, w.field, cols), O.rs_encode(w.field, w.n, w.k, elems(host, w.field, cols)))
+    mask = WL.erasure_mask(w.n, w.erasures, w.seed)
+    assert np.array_equal(gpu_decode(ctx, w.field, w.n, w.k, cw, mask), cw)
+
+
+def test_large_gf16_workload(ctx):
+    """n = 65536, k = 32768, 4 KiB shards: sampled parity rows and columns
+    against the oracle, then random and burst erasures of n - k rows recovered
+    on every byte."""
+    w = WL.WORKLOADS["large_gf16"]
+    host = message(w.n, w.k, w.shard_bytes, w.seed)
+    cw = gpu_encode(ctx, w.field, w.n, w.k, host)
+    assert np.array_equal(cw[: w.k], host[: w.k])
+    cols = elem_cols(w.shard_bytes, w.field, 3, seed=3)
+    rows = np.sort(np.random.default_rng(4).choice(np.arange(w.k, w.n), 12, replace=False))
+    ref = O.rs_encode(w.field, w.n, w.k, elems(host, w.field, cols), rows=rows)
+    assert np.array_equal(elems(cw, w.field, cols)[rows], ref[rows])
+    for mask in (WL.erasure_mask(w.n, w.erasures, w.seed),
+                 WL.burst_mask(w.n, w.erasures, 0),
+                 WL.burst_mask(w.n, w.erasures, WL.random_burst_start(w.n, w.erasures, w.seed))):
+        assert np.array_equal(gpu_decode(ctx, w.field, w.n, w.k, cw, mask), cw)
