@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Benchmark: systematic RS encode + erasure decode on one codeword.
+
+A step is one rs_encode followed by one rs_decode (every row of the hot path:
+precomputed tables, locator, Phi, inverse transform, derivative, transform,
+divide) on the workload large_gf16: GF(2^16), n = 65536, k = 32768, 4 KiB
+shards (128 MiB of message, 256 MiB codeword), n - k = 32768 erased rows at
+seeded random positions.  Inputs are resident in HBM when timing starts and the
+codeword (256 MiB) is larger than L2 (129 MB), so no L2 flush is needed.
+
+metric = shard-data GB/s: per step, k*S bytes of message encoded plus |E|*S
+bytes recovered, divided by the step time (whole job, all ranks).
+e2e = the same metric through the Python binding with host buffers: every
+step copies the message in from pinned host memory, encodes, copies the parity
+out, copies the received codeword in, decodes, and copies the codeword out.
+
+With --impl reference the CPU oracle (the plain-definition checker of this
+repository) is timed instead, on a bounded sample of the same workload.
+
+Multi-GPU: the path does not shard across GPUs by design (one GPU per
+codeword); N ranks run N independent replicas and the value is the total.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1404_3458_gb300 import workloads as WL  # noqa: E402
+
+METRIC = "encode/decode GB/s of shard data"
+UNIT = "GB/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="large_gf16", choices=sorted(WL.WORKLOADS))
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------- distributed
+
+def dist_setup(use_gpu: bool):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if use_gpu else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        top = max(sm)
+        loaded = [x for x in sm if x >= 0.5 * top] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- our arm
+
+def pct(xs, q):
+    xs = sorted(xs)
+    i = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[i]
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1404_3458_gb300 import lch
+
+    world, rank, local = dist_setup(True)
+    torch.cuda.set_device(local)
+    w = WL.WORKLOADS[args.workload]
+    r, n, k, S = w.field, w.n, w.k, w.shard_bytes
+    ctx = lch.Context(local)
+    stream = torch.cuda.current_stream()
+
+    host = np.zeros((n, S), dtype=np.uint8)
+    host[:k] = WL.shards(k, S, w.seed + rank)
+    mask = WL.erasure_mask(n, w.erasures, w.seed + 100 + rank)
+    ne = int(mask.sum())
+    buf = torch.from_numpy(host).cuda()
+    step_bytes = (k + ne) * S  # message encoded + data recovered
+
+    def step():
+        ctx.rs_encode(n, k, r, buf)
+        ctx.rs_decode(n, k, r, buf, mask)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # per-call latency (separate, event-timed)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
+    enc_ms, dec_ms = [], []
+    for i in range(args.steps):
+        ev[3 * i].record(stream)
+        ctx.rs_encode(n, k, r, buf)
+        ev[3 * i + 1].record(stream)
+        ctx.rs_decode(n, k, r, buf, mask)
+        ev[3 * i + 2].record(stream)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        enc_ms.append(ev[3 * i].elapsed_time(ev[3 * i + 1]))
+        dec_ms.append(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]))
+
+    # timed region: exactly K steps, profiling events on the launch stream
+    ctx.profile_enable(True)
+    launches0 = ctx.launches
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        start.record(stream)
+        for _ in range(args.steps):
+            step()
+        end.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    launches = ctx.launches - launches0
+    ms = start.elapsed_time(end)
+    kinds = {}
+    for kind, name in enumerate(["pass", "deriv", "rowscale", "locator"]):
+        kinds[name] = ctx.profile(kind)
+    ctx.profile_enable(False)
+    ms_max = max_over_ranks(ms, world)
+    value = world * step_bytes * args.steps / (ms_max / 1e3) / 1e9
+
+    # verify the last decode reproduced the encoded codeword
+    check = torch.from_numpy(host).cuda()
+    ctx.rs_encode(n, k, r, check)
+    torch.cuda.synchronize()
+    ok = bool(torch.equal(check, buf))
+
+    # dominant kernel roofline (transform pass)
+    hbm, hbm_src = peaks()
+    tot_ms = sum(v["ms"] for v in kinds.values())
+    dom = max(kinds, key=lambda kk: kinds[kk]["ms"])
+    d = kinds[dom]
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] else 0.0
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "peak_source": f"{hbm_src} hbm_gbs", "traffic": None,
+                "launches_per_step": d["launches"] / args.steps,
+                "share_of_kernel_time": round(d["ms"] / tot_ms, 4) if tot_ms else None}
+    alg_bytes = 2 * n * S  # encode n*S + decode n*S per step
+    step_ms = ms / args.steps
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(ctx, torch, host, mask, w, args)
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+        "config": {"workload": w.name, "field": f"GF(2^{r})", "n": n, "k": k, "shard_bytes": S,
+                   "erasures": ne, "erasure_pattern": "seeded uniform random",
+                   "step": "rs_encode + rs_decode", "l2": "inputs larger than L2 (256 MiB codeword), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "hbm_roofline_step": {"alg_bytes_per_step": alg_bytes,
+                              "achieved_gbs": round(alg_bytes / (step_ms / 1e3) / 1e9, 2),
+                              "frac": round(alg_bytes / (step_ms / 1e3) / 1e9 / hbm, 4)},
+        "latency_ms": {"encode_p50": round(pct(enc_ms, 50), 4), "encode_p99": round(pct(enc_ms, 99), 4),
+                       "decode_p50": round(pct(dec_ms, 50), 4), "decode_p99": round(pct(dec_ms, 99), 4)},
+        "kernels": {kk: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                         "gbs": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 2) if v["ms"] else None}
+                    for kk, v in kinds.items()},
+        "roofline": roofline,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "verified": ok,
+    }
+    if e2e:
+        out["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, n, k, S, ne)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def run_e2e(ctx, torch, host, mask, w, args):
+    r, n, k, S = w.field, w.n, w.k, w.shard_bytes
+    pin = torch.from_numpy(host).pin_memory()
+    out_host = torch.empty_like(pin).pin_memory()
+    dev = torch.empty((n, S), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    ne = int(mask.sum())
+
+    def step():
+        dev[:k].copy_(pin[:k], non_blocking=True)          # message in
+        ctx.rs_encode(n, k, r, dev)
+        out_host[k:].copy_(dev[k:], non_blocking=True)     # parity out
+        dev.copy_(pin, non_blocking=True)                  # received codeword in
+        ctx.rs_decode(n, k, r, dev, mask)
+        out_host.copy_(dev, non_blocking=True)             # codeword out
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 2)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    return {"value": round((k + ne) * S / (ms / 1e3) / 1e9, 3), "unit": UNIT,
+            "h2d_bytes_per_step": (k + n) * S, "d2h_bytes_per_step": (n - k + n) * S, "ms_per_step": round(ms, 4)}
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(w, n, k, S, ne, rows_per_call=8, cols=4, seed=0):
+    """Time the oracle on a bounded sample of one encode and one decode of the
+    workload: each call computes its barycentric weights over all k points
+    (a fixed per-call cost) and then `rows_per_call` rows of `cols` element
+    columns.  Returns (seconds, equivalent shard bytes of the sample)."""
+    from oracle import oracle as O
+
+    r = w.field
+    E = S // (r // 8)
+    g = np.random.default_rng(seed)
+    colsel = np.sort(g.choice(E, cols, replace=False))
+    host = np.zeros((n, S), dtype=np.uint8)
+    host[:k] = WL.shards(k, S, w.seed)
+    el = O.to_elems(host, r)[:, colsel].copy()
+    mask = WL.erasure_mask(n, w.erasures, w.seed + 100)
+    erow = np.nonzero(mask)[0]
+    prow = np.sort(g.choice(np.arange(k, n), rows_per_call, replace=False))
+    drow = np.sort(g.choice(erow, rows_per_call, replace=False))
+    t0 = time.perf_counter()
+    O.rs_encode(r, n, k, el, rows=prow)
+    t1 = time.perf_counter()
+    O.rs_decode(r, n, k, el, mask, rows=drow)
+    t2 = time.perf_counter()
+    # fraction of a full step that the sample represents, per call
+    f_enc = (rows_per_call * cols) / ((n - k) * E)
+    f_dec = (rows_per_call * cols) / (ne * E)
+    return t1 - t0, t2 - t1, f_enc * k * S, f_dec * ne * S
+
+
+def cpu_baseline(w, n, k, S, ne):
+    te, td, be, bd = oracle_sample(w, n, k, S, ne)
+    return {"value": round((be + bd) / (te + td) / 1e9, 12), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"one oracle encode (8 parity rows) and one decode (8 erased rows) of {w.name}, "
+                       f"4 element columns each; value = the sample's share of a step's shard data / its time "
+                       f"({te + td:.2f} s; each call also pays the O(k^2) barycentric weights)")}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(False)
+    if rank != 0:
+        return
+    w = WL.WORKLOADS[args.workload]
+    n, k, S = w.n, w.k, w.shard_bytes
+    ne = w.erasures
+    times, byts = [], []
+    for i in range(args.warmup + args.steps):
+        te, td, be, bd = oracle_sample(w, n, k, S, ne, rows_per_call=2, cols=2, seed=i)
+        if i >= args.warmup:
+            times.append(te + td)
+            byts.append(be + bd)
+    value = sum(byts) / sum(times) / 1e9
+    out = {"metric": METRIC, "value": round(value, 12), "unit": UNIT, "impl": "reference", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+           "data": "synthetic",
+           "config": {"workload": w.name, "field": f"GF(2^{w.field})", "n": n, "k": k, "shard_bytes": S,
+                      "erasures": ne, "step": "oracle rs_encode + rs_decode on a bounded sample"},
+           "cpu_baseline": {"value": round(value, 12), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "per step: one oracle encode and one decode of 2 rows x 2 element columns"},
+           "e2e": {"value": round(value, 12), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -124,6 +124,23 @@ LCH_API const char *lch_last_error(void);
 /* Number of kernels this context has launched so far (diagnostics). */
 LCH_API uint64_t lch_launch_count(const lch_ctx *ctx);
 
+/* Kernel kinds for the profiling counters. */
+#define LCH_KIND_PASS 0     /* transform butterfly pass (Sec. III.C / III.E) */
+#define LCH_KIND_DERIV 1    /* derivative neighbour sums (Sec. IV.B) */
+#define LCH_KIND_ROWSCALE 2 /* per-row scaling: Phi, B, B^-1, final divide */
+#define LCH_KIND_LOCATOR 3  /* FWHT locator (Appendix) */
+#define LCH_KIND_COUNT 4
+
+/* Diagnostics.  With profiling on, every kernel launch is bracketed by CUDA
+ * events recorded on its own stream; lch_profile_read() returns, per kind,
+ * the number of launches, their summed device time in milliseconds and the
+ * algorithmic bytes they moved (each launch counts the rows it must read and
+ * write once: 2 x rows x shard_bytes, plus rows x shard_bytes when it also
+ * reads its output).  Enabling (or re-enabling) clears the counters.
+ * Reading synchronises on the recorded events. */
+LCH_API int lch_profile_enable(lch_ctx *ctx, int on);
+LCH_API int lch_profile_read(lch_ctx *ctx, int kind, uint64_t *launches, double *total_ms, uint64_t *bytes);
+
 #ifdef __cplusplus
 }
 #endif

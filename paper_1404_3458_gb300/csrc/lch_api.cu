@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/lch.h"
 #include "lch_internal.cuh"
@@ -18,6 +19,15 @@ struct lch_ctx {
     uint8_t *scratch = nullptr;  // grows on demand
     size_t scratch_bytes = 0;
     uint64_t launches = 0;
+    // profiling: event pairs around launches (reused across enables)
+    struct Rec {
+        cudaEvent_t a, b;
+        int kind;
+        uint64_t bytes;
+    };
+    bool prof_on = false;
+    std::vector<Rec> prof;
+    size_t prof_used = 0;
 };
 
 namespace {
@@ -134,6 +144,36 @@ int ensure_fl(lch_ctx *ctx, int field, uint32_t lgn, uint32_t *work, cudaStream_
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Profiling brackets around one launch (no-ops unless enabled).
+lch_ctx::Rec *prof_begin(lch_ctx *ctx, cudaStream_t s)
+{
+    if (!ctx->prof_on) return nullptr;
+    if (ctx->prof_used == ctx->prof.size()) {
+        lch_ctx::Rec r{};
+        if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return nullptr;
+        ctx->prof.push_back(r);
+    }
+    lch_ctx::Rec *r = &ctx->prof[ctx->prof_used++];
+    cudaEventRecord(r->a, s);
+    return r;
+}
+
+void prof_end(lch_ctx::Rec *r, cudaStream_t s, int kind, uint64_t bytes)
+{
+    if (!r) return;
+    r->kind = kind;
+    r->bytes = bytes;
+    cudaEventRecord(r->b, s);
+}
+
+#define PROF(kind, bytes, call)                                                                    \
+    do {                                                                                           \
+        lch_ctx::Rec *pr_ = prof_begin(ctx, s);                                                    \
+        cudaError_t e_ = (call);                                                                   \
+        prof_end(pr_, s, kind, bytes);                                                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);                                       \
+    } while (0)
+
 // Levels [0, lgh) are split into at most two passes of <= 8 levels each.
 void split_levels(uint32_t lgh, uint32_t *a, uint32_t *b)
 {
@@ -170,16 +210,17 @@ int transform(lch_ctx *ctx, int field, uint32_t h, uint32_t l, int inverse, cons
         first_L0 = 0;
         first_n = a;
     }
+    const uint64_t bytes = 2ull * h * S;
     p.src = src;
     p.dst = dst;
     p.L0 = first_L0;
     p.nlev = first_n;
-    CU(launch_pass(field, p, s, &ctx->launches), "transform pass");
+    PROF(LCH_KIND_PASS, bytes, launch_pass(field, p, s, &ctx->launches));
     if (b) {
         p.src = dst;
         p.L0 = second_L0;
         p.nlev = second_n;
-        CU(launch_pass(field, p, s, &ctx->launches), "transform pass");
+        PROF(LCH_KIND_PASS, bytes, launch_pass(field, p, s, &ctx->launches));
     }
     return LCH_OK;
 }
@@ -194,7 +235,7 @@ int derivative(lch_ctx *ctx, int field, uint32_t h, uint8_t *src, uint8_t *dst, 
         return LCH_OK;
     }
     // d^d_i = d_i B_i (eq. dimathrmd)
-    CU(launch_rowscale(field, src, src, S, h, t.B, 0, s, &ctx->launches), "derivative scale");
+    PROF(LCH_KIND_ROWSCALE, 2ull * h * S, launch_rowscale(field, src, src, S, h, t.B, 0, s, &ctx->launches));
     uint32_t a, b;
     split_levels(lgh, &a, &b);
     SupersetArgs q;
@@ -205,15 +246,15 @@ int derivative(lch_ctx *ctx, int field, uint32_t h, uint8_t *src, uint8_t *dst, 
     q.L0 = 0;
     q.nlev = a;
     q.accumulate = 0;
-    CU(launch_superset(q, s, &ctx->launches), "derivative sums");
+    PROF(LCH_KIND_DERIV, 2ull * h * S, launch_superset(q, s, &ctx->launches));
     if (b) {
         q.L0 = a;
         q.nlev = b;
         q.accumulate = 1;
-        CU(launch_superset(q, s, &ctx->launches), "derivative sums");
+        PROF(LCH_KIND_DERIV, 3ull * h * S, launch_superset(q, s, &ctx->launches));
     }
     // divide coefficient j by B_j (eq. XDhx3)
-    CU(launch_rowscale(field, dst, dst, S, h, t.Binv, 0, s, &ctx->launches), "derivative scale");
+    PROF(LCH_KIND_ROWSCALE, 2ull * h * S, launch_rowscale(field, dst, dst, S, h, t.Binv, 0, s, &ctx->launches));
     return LCH_OK;
 }
 
@@ -247,10 +288,10 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
     if (rc) return rc;
     const FieldTables &t = ctx->tab[field == LCH_GF16];
     // Step 1: Pi(j) off E and 1/Pi'(j) on E.
-    CU(launch_locator(field, t, lgn, bits, ctx->fl[field == LCH_GF16][lgn], work, pre, post, s, &ctx->launches),
-       "locator");
+    PROF(LCH_KIND_LOCATOR, 0, launch_locator(field, t, lgn, bits, ctx->fl[field == LCH_GF16][lgn], work, pre, post, s, &ctx->launches));
     // Step 2: Phi = F * Pi, zero on erased rows (eq. hatF(l)).
-    CU(launch_rowscale(field, phi, shards, S, n, pre, 0, s, &ctx->launches), "Phi");
+    PROF(LCH_KIND_ROWSCALE, (uint64_t)(n - ne) * S + (uint64_t)n * S,
+         launch_rowscale(field, phi, shards, S, n, pre, 0, s, &ctx->launches));
     // Step 3: coefficients of hatF.
     rc = transform(ctx, field, n, 0, 1, phi, phi, S, s);
     if (rc) return rc;
@@ -261,7 +302,7 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
     rc = transform(ctx, field, n, 0, 0, phi2, phi2, S, s);
     if (rc) return rc;
     // Step 6: F(j) = hatF'(j) / Pi'(j), written to the erased rows only.
-    CU(launch_rowscale(field, shards, phi2, S, n, post, 1, s, &ctx->launches), "erasures");
+    PROF(LCH_KIND_ROWSCALE, 2ull * ne * S, launch_rowscale(field, shards, phi2, S, n, post, 1, s, &ctx->launches));
     return LCH_OK;
 }
 
@@ -333,6 +374,10 @@ LCH_API void lch_ctx_destroy(lch_ctx *ctx)
         for (auto &row : ctx->fl)
             for (auto *p : row) cudaFree(p);
         cudaFree(ctx->scratch);
+        for (auto &r : ctx->prof) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
     }
     delete ctx;
 }
@@ -422,5 +467,36 @@ LCH_API const char *lch_strerror(int status)
 LCH_API const char *lch_last_error(void) { return g_err; }
 
 LCH_API uint64_t lch_launch_count(const lch_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+LCH_API int lch_profile_enable(lch_ctx *ctx, int on)
+{
+    if (!ctx) return fail(LCH_EINVAL, "ctx is NULL");
+    ctx->prof_on = on != 0;
+    ctx->prof_used = 0;
+    return LCH_OK;
+}
+
+LCH_API int lch_profile_read(lch_ctx *ctx, int kind, uint64_t *launches, double *total_ms, uint64_t *bytes)
+{
+    if (!ctx || !launches || !total_ms || !bytes) return fail(LCH_EINVAL, "NULL argument");
+    if (kind < 0 || kind >= LCH_KIND_COUNT) return fail(LCH_EINVAL, "unknown kernel kind %d", kind);
+    DeviceScope ds(ctx->device);
+    uint64_t n = 0, by = 0;
+    double ms = 0;
+    for (size_t i = 0; i < ctx->prof_used; i++) {
+        const lch_ctx::Rec &r = ctx->prof[i];
+        if (r.kind != kind) continue;
+        CU(cudaEventSynchronize(r.b), "cudaEventSynchronize");
+        float t = 0;
+        CU(cudaEventElapsedTime(&t, r.a, r.b), "cudaEventElapsedTime");
+        n++;
+        ms += t;
+        by += r.bytes;
+    }
+    *launches = n;
+    *total_ms = ms;
+    *bytes = by;
+    return LCH_OK;
+}
 
 } // extern "C"

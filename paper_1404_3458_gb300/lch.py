@@ -57,6 +57,9 @@ def load() -> ctypes.CDLL:
         "lch_strerror": (ctypes.c_char_p, [i]),
         "lch_last_error": (ctypes.c_char_p, []),
         "lch_launch_count": (ctypes.c_uint64, [vp]),
+        "lch_profile_enable": (i, [vp, i]),
+        "lch_profile_read": (i, [vp, i, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_uint64)]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -119,6 +122,16 @@ class Context:
     @property
     def launches(self) -> int:
         return int(load().lch_launch_count(self._h))
+
+    def profile_enable(self, on: bool = True):
+        _check(load().lch_profile_enable(self._h, int(on)))
+
+    def profile(self, kind: int) -> dict:
+        """Launches, summed device ms and algorithmic bytes of one kernel kind
+        since profiling was enabled (see lch_profile_read)."""
+        n, ms, by = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_uint64()
+        _check(load().lch_profile_read(self._h, kind, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
+        return {"launches": int(n.value), "ms": float(ms.value), "bytes": int(by.value)}
 
     # Sec. III: Psi_h^l and its inverse, in place on h rows.
     def fft(self, field: int, l: int, buf, stream=None):
