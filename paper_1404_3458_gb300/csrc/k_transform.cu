@@ -23,19 +23,173 @@ constexpr int kThreads = 256;
 constexpr uint32_t kTileBytes = 32768; // data bytes per tile
 constexpr int kTargetCtas = 152 * 8;
 
-__host__ __device__ __forceinline__ uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
 // First record of local level s among the 2^nlev - 1 records of a tile.
 __device__ __forceinline__ uint32_t rec_base(uint32_t nrows, uint32_t s) { return nrows - (nrows >> s); }
 
-template <int R, int INV>
-__global__ void __launch_bounds__(kThreads) k_pass(PassArgs a, uint32_t lg_cw)
+// Shared-memory layout of a tile's factor records (nrec of them):
+//   GF(2^16): region 0 = nrec x 128 B (c*e, e < 64), region 1 = nrec x 128 B
+//             (c*(e<<6)), region 2 = nrec x 32 B (c*(e<<12), e < 16);
+//   GF(2^8):  nrec x 256 B (c*e).
+// Every sub-table starts at a multiple of its own size, so a lookup address
+// is (scaled index) | (sub-table base): one LOP3, no add.
+template <int R> struct TabRef;
+template <> struct TabRef<16> {
+    uint32_t b0, b1, b2;
+};
+template <> struct TabRef<8> {
+    uint32_t b0;
+};
+
+template <int R> __device__ __forceinline__ TabRef<R> tab_ref(uint32_t q, uint32_t nrec);
+template <> __device__ __forceinline__ TabRef<16> tab_ref<16>(uint32_t q, uint32_t nrec)
 {
-    extern __shared__ __align__(16) uint8_t sm[];
+    return {q << 7, (nrec + q) << 7, (nrec << 8) + (q << 5)};
+}
+template <> __device__ __forceinline__ TabRef<8> tab_ref<8>(uint32_t q, uint32_t)
+{
+    return {q << 8};
+}
+
+// c * w for the two GF(2^16) elements packed in w; `off` is a compile-time
+// multiple of 128 (resp. 32 for region 2) added to every base.
+template <uint32_t OFF0, uint32_t OFF2>
+__device__ __forceinline__ uint32_t mul16(const uint8_t *tab, uint32_t w, const TabRef<16> &t)
+{
+    const uint32_t t0 = *reinterpret_cast<const uint16_t *>(tab + ((((w << 1) & 0x7Eu) | t.b0) + OFF0));
+    const uint32_t t1 = *reinterpret_cast<const uint16_t *>(tab + ((((w >> 5) & 0x7Eu) | t.b1) + OFF0));
+    const uint32_t t2 = *reinterpret_cast<const uint16_t *>(tab + ((((w >> 11) & 0x1Eu) | t.b2) + OFF2));
+    const uint32_t t3 = *reinterpret_cast<const uint16_t *>(tab + ((((w >> 15) & 0x7Eu) | t.b0) + OFF0));
+    const uint32_t t4 = *reinterpret_cast<const uint16_t *>(tab + ((((w >> 21) & 0x7Eu) | t.b1) + OFF0));
+    const uint32_t t5 = *reinterpret_cast<const uint16_t *>(tab + ((((w >> 27) & 0x1Eu) | t.b2) + OFF2));
+    return (t0 ^ t1 ^ t2) | ((t3 ^ t4 ^ t5) << 16);
+}
+
+template <uint32_t OFF0>
+__device__ __forceinline__ uint32_t mul8(const uint8_t *tab, uint32_t w, const TabRef<8> &t)
+{
+    const uint32_t r0 = tab[((w & 0xFFu) | t.b0) + OFF0];
+    const uint32_t r1 = tab[(((w >> 8) & 0xFFu) | t.b0) + OFF0];
+    const uint32_t r2 = tab[(((w >> 16) & 0xFFu) | t.b0) + OFF0];
+    const uint32_t r3 = tab[((w >> 24) | t.b0) + OFF0];
+    return r0 | (r1 << 8) | (r2 << 16) | (r3 << 24);
+}
+
+// Multiply by the record that is `K` records after the one t points to.
+template <int R, uint32_t K> struct MulK;
+template <uint32_t K> struct MulK<16, K> {
+    static __device__ __forceinline__ uint32_t f(const uint8_t *tab, uint32_t w, const TabRef<16> &t)
+    {
+        return mul16<K * 128, K * 32>(tab, w, t);
+    }
+};
+template <uint32_t K> struct MulK<8, K> {
+    static __device__ __forceinline__ uint32_t f(const uint8_t *tab, uint32_t w, const TabRef<8> &t)
+    {
+        return mul8<K * 256>(tab, w, t);
+    }
+};
+
+// Butterflies of local level j (0 <= j < Q) on the 2^Q registers x[], whose
+// row u is tile row base | (u << s0).  The pair (u, u + 2^j) belongs to block
+// (base >> (s0+j+1)) + (u >> (j+1)) of level s0 + j.
+template <int R, int INV, int Q, int J, int U>
+struct LevelStep {
+    static __device__ __forceinline__ void run(uint32_t *x, const uint8_t *tab, const TabRef<R> &t)
+    {
+        if constexpr (U < (1 << Q)) {
+            if constexpr ((U & (1 << J)) == 0) {
+                constexpr uint32_t K = (uint32_t)(U >> (J + 1));
+                uint32_t &A = x[U];
+                uint32_t &B = x[U | (1 << J)];
+                if constexpr (INV) {
+                    B ^= A;
+                    A ^= MulK<R, K>::f(tab, B, t);
+                } else {
+                    A ^= MulK<R, K>::f(tab, B, t);
+                    B ^= A;
+                }
+            }
+            LevelStep<R, INV, Q, J, U + 1>::run(x, tab, t);
+        }
+    }
+};
+
+template <int R, int INV, int Q, int JJ>
+__device__ __forceinline__ void round_levels(uint32_t *x, const uint8_t *tab, uint32_t nrec, uint32_t nrows,
+                                             uint32_t base, uint32_t s0)
+{
+    if constexpr (JJ < Q) {
+        constexpr int J = INV ? JJ : Q - 1 - JJ;
+        const uint32_t s = s0 + J;
+        const uint32_t q = rec_base(nrows, s) + (base >> (s + 1));
+        const TabRef<R> t = tab_ref<R>(q, nrec);
+        LevelStep<R, INV, Q, J, 0>::run(x, tab, t);
+        round_levels<R, INV, Q, JJ + 1>(x, tab, nrec, nrows, base, s0);
+    }
+}
+
+// One round: every thread takes 2^Q rows (bits s0 .. s0+Q-1 free) of one
+// column word, runs Q levels in registers and writes the rows back.
+template <int R, int INV, int Q>
+__device__ __forceinline__ void round_q(uint32_t *data, const uint8_t *tab, uint32_t nrec, uint32_t nrows,
+                                        uint32_t lg_w, uint32_t s0)
+{
+    const uint32_t W = 1u << lg_w;
+    const uint32_t items = (nrows >> Q) << lg_w;
+    const uint32_t stride = 1u << (s0 + lg_w);
+    for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
+        const uint32_t g = it >> lg_w, w = it & (W - 1u);
+        const uint32_t base = ((g >> s0) << (s0 + Q)) | (g & ((1u << s0) - 1u));
+        uint32_t *p = data + (base << lg_w) + w;
+        uint32_t x[1 << Q];
+#pragma unroll
+        for (int u = 0; u < (1 << Q); u++) x[u] = p[u * stride];
+        round_levels<R, INV, Q, 0>(x, tab, nrec, nrows, base, s0);
+#pragma unroll
+        for (int u = 0; u < (1 << Q); u++) p[u * stride] = x[u];
+    }
+}
+
+template <int R, int INV>
+__device__ __forceinline__ void run_round(uint32_t q, uint32_t *data, const uint8_t *tab, uint32_t nrec,
+                                          uint32_t nrows, uint32_t lg_w, uint32_t s0)
+{
+    switch (q) {
+    case 1: round_q<R, INV, 1>(data, tab, nrec, nrows, lg_w, s0); break;
+    case 2: round_q<R, INV, 2>(data, tab, nrec, nrows, lg_w, s0); break;
+    case 3: round_q<R, INV, 3>(data, tab, nrec, nrows, lg_w, s0); break;
+    default: round_q<R, INV, 4>(data, tab, nrec, nrows, lg_w, s0); break;
+    }
+}
+
+template <int R>
+__host__ __device__ __forceinline__ uint32_t tab_bytes(uint32_t nrec)
+{
+    return (nrec * FT<R>::rec_bytes + 127u) & ~127u;
+}
+
+// Copy record q (global layout: the rec_bytes of one record back to back)
+// into the region layout above, 16 bytes per thread step.
+template <int R>
+__device__ __forceinline__ void stage_chunk(uint8_t *tab, uint32_t nrec, uint32_t q, uint32_t c, const uint4 *src)
+{
+    uint32_t dst;
+    if constexpr (R == 16)
+        dst = c < 8 ? (q << 7) + (c << 4) : (c < 16 ? ((nrec + q) << 7) + ((c - 8) << 4) : (nrec << 8) + (q << 5) + ((c - 16) << 4));
+    else
+        dst = (q << 8) + (c << 4);
+    *reinterpret_cast<uint4 *>(tab + dst) = src[c];
+}
+
+template <int R, int INV>
+__global__ void __launch_bounds__(kThreads, 2) k_pass(PassArgs a, uint32_t lg_cw)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
     const uint32_t nlev = a.nlev, nrows = 1u << nlev, nrec = nrows - 1;
     uint8_t *tab = sm;
-    uint32_t *data = reinterpret_cast<uint32_t *>(sm + align16(nrec * FT<R>::rec_bytes));
-    const uint32_t cw = 1u << lg_cw, lg_wpr = lg_cw - 2, wpr = 1u << lg_wpr, lg_vpr = lg_cw - 4;
+    uint32_t *data = reinterpret_cast<uint32_t *>(sm + tab_bytes<R>(nrec));
+    const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
     const uint32_t g = blockIdx.x;
     const uint32_t lo = g & ((1u << a.L0) - 1u);
     const uint32_t hibase = (g >> a.L0) << (a.L0 + nlev);
@@ -43,56 +197,47 @@ __global__ void __launch_bounds__(kThreads) k_pass(PassArgs a, uint32_t lg_cw)
     // Stage the factor records of this row group.
     constexpr uint32_t cpr = FT<R>::rec_bytes / 16;
     for (uint32_t v = threadIdx.x; v < nrec * cpr; v += blockDim.x) {
-        uint32_t q = v / cpr, c = v - q * cpr;
+        const uint32_t q = v / cpr, c = v - q * cpr;
         uint32_t s = 0;
         while (q >= rec_base(nrows, s + 1)) s++;
-        uint32_t beta = q - rec_base(nrows, s);
-        uint32_t i = a.L0 + s;
-        uint32_t y = ((hibase | (beta << (i + 1))) ^ a.l) >> i;
-        const uint4 *src = reinterpret_cast<const uint4 *>(a.rec + (size_t)(level_off(R, i) + y) * FT<R>::rec_bytes);
-        reinterpret_cast<uint4 *>(tab + q * FT<R>::rec_bytes)[c] = src[c];
+        const uint32_t beta = q - rec_base(nrows, s);
+        const uint32_t i = a.L0 + s;
+        const uint32_t y = ((hibase | (beta << (i + 1))) ^ a.l) >> i;
+        stage_chunk<R>(tab, nrec, q, c,
+                       reinterpret_cast<const uint4 *>(a.rec + (size_t)(level_off(R, i) + y) * FT<R>::rec_bytes));
     }
 
-    const uint32_t items = (nrows >> 1) << lg_wpr;
+    const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, qb = nlev - qa;
     for (size_t col = (size_t)blockIdx.y * cw; col < a.S; col += (size_t)gridDim.y * cw) {
         const size_t rem = a.S - col;
         const uint32_t width = rem < cw ? (uint32_t)rem : cw;
         __syncthreads();
         for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
-            uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
+            const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
             if (c * 16 < width) {
-                size_t t = hibase | ((size_t)m << a.L0) | lo;
-                reinterpret_cast<uint4 *>(data)[v] =
-                    *reinterpret_cast<const uint4 *>(a.src + t * a.S + col + c * 16);
+                const size_t t = hibase | ((size_t)m << a.L0) | lo;
+                reinterpret_cast<uint4 *>(data)[v] = *reinterpret_cast<const uint4 *>(a.src + t * a.S + col + c * 16);
             }
         }
         __syncthreads();
-        for (uint32_t k = 0; k < nlev; k++) {
-            const uint32_t s = INV ? k : nlev - 1 - k;
-            for (uint32_t q = threadIdx.x; q < items; q += blockDim.x) {
-                uint32_t p = q >> lg_wpr, w = q & (wpr - 1u);
-                uint32_t beta = p >> s, off = p & ((1u << s) - 1u);
-                uint32_t m = (beta << (s + 1)) | off;
-                const uint8_t *T = tab + (rec_base(nrows, s) + beta) * FT<R>::rec_bytes;
-                uint32_t *pa = data + (m << lg_wpr) + w;
-                uint32_t *pb = pa + ((1u << s) << lg_wpr);
-                uint32_t x = *pa, y = *pb;
-                if (INV) {
-                    y ^= x;
-                    x ^= mul_word<R>(y, T);
-                } else {
-                    x ^= mul_word<R>(y, T);
-                    y ^= x;
-                }
-                *pa = x;
-                *pb = y;
+        if (INV) {
+            run_round<R, INV>(qa, data, tab, nrec, nrows, lg_w, 0);
+            if (qb) {
+                __syncthreads();
+                run_round<R, INV>(qb, data, tab, nrec, nrows, lg_w, qa);
             }
-            __syncthreads();
+        } else {
+            if (qb) {
+                run_round<R, INV>(qb, data, tab, nrec, nrows, lg_w, qa);
+                __syncthreads();
+            }
+            run_round<R, INV>(qa, data, tab, nrec, nrows, lg_w, 0);
         }
+        __syncthreads();
         for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
-            uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
+            const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
             if (c * 16 < width) {
-                size_t t = hibase | ((size_t)m << a.L0) | lo;
+                const size_t t = hibase | ((size_t)m << a.L0) | lo;
                 *reinterpret_cast<uint4 *>(a.dst + t * a.S + col + c * 16) = reinterpret_cast<const uint4 *>(data)[v];
             }
         }
@@ -101,7 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_pass(PassArgs a, uint32_t lg_cw)
 
 __global__ void __launch_bounds__(kThreads) k_superset(SupersetArgs a, uint32_t lg_cw)
 {
-    extern __shared__ __align__(16) uint8_t sm[];
+    extern __shared__ __align__(128) uint8_t sm[];
     uint32_t *data = reinterpret_cast<uint32_t *>(sm);
     const uint32_t nlev = a.nlev, nrows = 1u << nlev;
     const uint32_t cw = 1u << lg_cw, lg_wpr = lg_cw - 2, wpr = 1u << lg_wpr, lg_vpr = lg_cw - 4;
@@ -193,7 +338,7 @@ cudaError_t pass_impl(const PassArgs &a, cudaStream_t s)
 {
     const uint32_t nrows = 1u << a.nlev;
     const uint32_t lg_cw = pick_lg_cw(nrows, a.S);
-    const size_t smem = align16((nrows - 1) * FT<R>::rec_bytes) + ((size_t)nrows << lg_cw);
+    const size_t smem = tab_bytes<R>(nrows - 1) + ((size_t)nrows << lg_cw);
     dim3 grid = pick_grid(a.h >> a.nlev, a.S, lg_cw);
     k_pass<R, INV><<<grid, kThreads, smem, s>>>(a, lg_cw);
     return cudaGetLastError();
