@@ -91,6 +91,21 @@ LCH_API int lch_ifft(lch_ctx *ctx, int field, uint32_t h, uint32_t l, void *buf,
 LCH_API int lch_derivative(lch_ctx *ctx, int field, uint32_t h, void *buf, size_t shard_bytes,
                            void *stream);
 
+/* lch_derivative without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * (a host application whose allocator owns the whole device heap, a plugin
+ * that its host forbids to allocate, or a latency-critical loop that cannot
+ * afford the implicit synchronisation of cudaMalloc/cudaFree).  It computes the
+ * same result as lch_derivative but takes no context: its scratch (at most
+ * 16 MiB, so h * shard_bytes <= 16777216, else LCH_EINVAL) and its B tables
+ * are file-scope device arrays that every GPU loading the library keeps until
+ * the process exits.  It runs on the current CUDA device.  The first call on a
+ * device sets those arrays up and synchronises `stream` once; make that first
+ * call before any stream capture.  All calls on a device share the scratch
+ * (which keeps the last call's contents); calls that overlap on the GPU race.
+ * Argument rules, layout and errors are otherwise those of lch_derivative. */
+LCH_API int lch_derivative_noalloc(int field, uint32_t h, void *buf, size_t shard_bytes, void *stream);
+
 /* Systematic (n, k) Reed-Solomon encoding (Sec. V, Algorithm 1).
  * shards holds n rows; rows 0..k-1 are the message m_0..m_{k-1} and are only
  * read; rows k..n-1 are overwritten with F(w_k)..F(w_{n-1}), where F is the

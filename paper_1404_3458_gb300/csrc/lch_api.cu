@@ -336,6 +336,8 @@ int encode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
 
 } // namespace
 
+void lch::set_last_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 extern "C" {
 
 LCH_API int lch_ctx_create(lch_ctx **out, int device)

@@ -123,6 +123,9 @@ struct FieldTables {
 
 cudaError_t build_field_tables(FieldTables &t, int r, cudaStream_t s, uint64_t *launches);
 
+// Record the text that lch_last_error() returns on this host thread.
+void set_last_error(const char *msg);
+
 // Opt the large-shared-memory kernels in on the current device.
 cudaError_t configure_transform_kernels();
 

@@ -57,6 +57,7 @@ def load() -> ctypes.CDLL:
         "lch_strerror": (ctypes.c_char_p, [i]),
         "lch_last_error": (ctypes.c_char_p, []),
         "lch_launch_count": (ctypes.c_uint64, [vp]),
+        "lch_derivative_noalloc": (i, [i, u32, vp, sz, vp]),
         "lch_profile_enable": (i, [vp, i]),
         "lch_profile_read": (i, [vp, i, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_uint64)]),
@@ -96,6 +97,14 @@ def _buf(t, rows=None):
     if rows is not None and t.shape[0] != rows:
         raise ValueError(f"expected {rows} rows, got {t.shape[0]}")
     return ctypes.c_void_p(t.data_ptr()), t.shape[1]
+
+
+def derivative_noalloc(field: int, buf, stream=None):
+    """lch_derivative_noalloc: the formal derivative of the h rows of ``buf``
+    in place, on the tensor's current device, without any device allocation
+    (for callers that cannot call cudaMalloc).  h * shard_bytes <= 16 MiB."""
+    p, S = _buf(buf)
+    _check(load().lch_derivative_noalloc(field, buf.shape[0], p, S, _stream_handle(stream)))
 
 
 class Context:
