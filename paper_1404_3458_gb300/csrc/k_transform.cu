@@ -20,8 +20,10 @@ namespace lch {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kPassThreads = 512;
 constexpr uint32_t kTileBytes = 32768; // data bytes per tile
 constexpr int kTargetCtas = 152 * 8;
+constexpr int kSms = 152;
 
 
 // First record of local level s among the 2^nlev - 1 records of a tile.
@@ -182,19 +184,34 @@ __device__ __forceinline__ void stage_chunk(uint8_t *tab, uint32_t nrec, uint32_
     *reinterpret_cast<uint4 *>(tab + dst) = src[c];
 }
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// One CTA per SM: the factor records of a row group stay in shared memory
+// while the CTA walks its column tiles; tile t+1 is copied in (cp.async)
+// while tile t is transformed.
 template <int R, int INV>
-__global__ void __launch_bounds__(kThreads, 2) k_pass(PassArgs a, uint32_t lg_cw)
+__global__ void __launch_bounds__(kPassThreads, 1) k_pass(PassArgs a, uint32_t lg_cw)
 {
     extern __shared__ __align__(128) uint8_t sm[];
     const uint32_t nlev = a.nlev, nrows = 1u << nlev, nrec = nrows - 1;
     uint8_t *tab = sm;
-    uint32_t *data = reinterpret_cast<uint32_t *>(sm + tab_bytes<R>(nrec));
     const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
+    uint8_t *const buf0 = sm + tab_bytes<R>(nrec);
+    const uint32_t tile_bytes = nrows << lg_cw;
     const uint32_t g = blockIdx.x;
     const uint32_t lo = g & ((1u << a.L0) - 1u);
     const uint32_t hibase = (g >> a.L0) << (a.L0 + nlev);
+    const size_t col_step = (size_t)gridDim.y << lg_cw;
+    const size_t col0 = (size_t)blockIdx.y << lg_cw;
+    const uint32_t ntiles = col0 < a.S ? (uint32_t)((a.S - col0 + col_step - 1) / col_step) : 0;
 
-    // Stage the factor records of this row group.
+    // Stage the factor records of this row group (first copy group).
     constexpr uint32_t cpr = FT<R>::rec_bytes / 16;
     for (uint32_t v = threadIdx.x; v < nrec * cpr; v += blockDim.x) {
         const uint32_t q = v / cpr, c = v - q * cpr;
@@ -203,22 +220,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_pass(PassArgs a, uint32_t lg_cw
         const uint32_t beta = q - rec_base(nrows, s);
         const uint32_t i = a.L0 + s;
         const uint32_t y = ((hibase | (beta << (i + 1))) ^ a.l) >> i;
-        stage_chunk<R>(tab, nrec, q, c,
-                       reinterpret_cast<const uint4 *>(a.rec + (size_t)(level_off(R, i) + y) * FT<R>::rec_bytes));
+        const uint8_t *src = a.rec + (size_t)(level_off(R, i) + y) * FT<R>::rec_bytes + c * 16;
+        uint32_t dst;
+        if constexpr (R == 16)
+            dst = c < 8 ? (q << 7) + (c << 4)
+                        : (c < 16 ? ((nrec + q) << 7) + ((c - 8) << 4) : (nrec << 8) + (q << 5) + ((c - 16) << 4));
+        else
+            dst = (q << 8) + (c << 4);
+        cp_async16(tab + dst, src);
     }
 
-    const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, qb = nlev - qa;
-    for (size_t col = (size_t)blockIdx.y * cw; col < a.S; col += (size_t)gridDim.y * cw) {
+    auto issue = [&](uint32_t t, uint32_t *dstbuf) {
+        const size_t col = col0 + (size_t)t * col_step;
         const size_t rem = a.S - col;
         const uint32_t width = rem < cw ? (uint32_t)rem : cw;
-        __syncthreads();
         for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
             const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
             if (c * 16 < width) {
-                const size_t t = hibase | ((size_t)m << a.L0) | lo;
-                reinterpret_cast<uint4 *>(data)[v] = *reinterpret_cast<const uint4 *>(a.src + t * a.S + col + c * 16);
+                const size_t row = hibase | ((size_t)m << a.L0) | lo;
+                cp_async16(reinterpret_cast<uint8_t *>(dstbuf) + v * 16, a.src + row * a.S + col + c * 16);
             }
         }
+    };
+
+    if (ntiles > 0) issue(0, reinterpret_cast<uint32_t *>(buf0));
+    cp_async_commit();
+    if (ntiles > 1) issue(1, reinterpret_cast<uint32_t *>(buf0 + tile_bytes));
+    cp_async_commit();
+
+    const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, qb = nlev - qa;
+    for (uint32_t t = 0; t < ntiles; t++) {
+        uint32_t *data = reinterpret_cast<uint32_t *>(buf0 + (t & 1u) * tile_bytes);
+        cp_async_wait1(); // tile t (and the records) have landed for this thread
         __syncthreads();
         if (INV) {
             run_round<R, INV>(qa, data, tab, nrec, nrows, lg_w, 0);
@@ -234,22 +267,31 @@ __global__ void __launch_bounds__(kThreads, 2) k_pass(PassArgs a, uint32_t lg_cw
             run_round<R, INV>(qa, data, tab, nrec, nrows, lg_w, 0);
         }
         __syncthreads();
-        for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
-            const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
-            if (c * 16 < width) {
-                const size_t t = hibase | ((size_t)m << a.L0) | lo;
-                *reinterpret_cast<uint4 *>(a.dst + t * a.S + col + c * 16) = reinterpret_cast<const uint4 *>(data)[v];
+        {
+            const size_t col = col0 + (size_t)t * col_step;
+            const size_t rem = a.S - col;
+            const uint32_t width = rem < cw ? (uint32_t)rem : cw;
+            for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
+                const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
+                if (c * 16 < width) {
+                    const size_t row = hibase | ((size_t)m << a.L0) | lo;
+                    *reinterpret_cast<uint4 *>(a.dst + row * a.S + col + c * 16) =
+                        reinterpret_cast<const uint4 *>(data)[v];
+                }
             }
         }
+        __syncthreads(); // everyone has read this buffer
+        if (t + 2 < ntiles) issue(t + 2, data);
+        cp_async_commit();
     }
 }
 
 __global__ void __launch_bounds__(kThreads) k_superset(SupersetArgs a, uint32_t lg_cw)
 {
     extern __shared__ __align__(128) uint8_t sm[];
-    uint32_t *data = reinterpret_cast<uint32_t *>(sm);
+    uint4 *data = reinterpret_cast<uint4 *>(sm);
     const uint32_t nlev = a.nlev, nrows = 1u << nlev;
-    const uint32_t cw = 1u << lg_cw, lg_wpr = lg_cw - 2, wpr = 1u << lg_wpr, lg_vpr = lg_cw - 4;
+    const uint32_t cw = 1u << lg_cw, lg_vpr = lg_cw - 4, vpr = 1u << lg_vpr;
     const uint32_t g = blockIdx.x;
     const uint32_t lo = g & ((1u << a.L0) - 1u);
     const uint32_t hibase = (g >> a.L0) << (a.L0 + nlev);
@@ -258,23 +300,35 @@ __global__ void __launch_bounds__(kThreads) k_superset(SupersetArgs a, uint32_t 
         const uint32_t width = rem < cw ? (uint32_t)rem : cw;
         __syncthreads();
         for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
-            uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
+            const uint32_t m = v >> lg_vpr, c = v & (vpr - 1u);
             if (c * 16 < width) {
-                size_t t = hibase | ((size_t)m << a.L0) | lo;
-                reinterpret_cast<uint4 *>(data)[v] =
-                    *reinterpret_cast<const uint4 *>(a.src + t * a.S + col + c * 16);
+                const size_t t = hibase | ((size_t)m << a.L0) | lo;
+                data[v] = *reinterpret_cast<const uint4 *>(a.src + t * a.S + col + c * 16);
             }
         }
         __syncthreads();
-        for (uint32_t q = threadIdx.x; q < (nrows << lg_wpr); q += blockDim.x) {
-            uint32_t m = q >> lg_wpr, w = q & (wpr - 1u);
-            if (w * 4 >= width) continue;
-            uint32_t acc = 0;
-            for (uint32_t s = 0; s < nlev; s++)
-                if (!((m >> s) & 1u)) acc ^= data[((m | (1u << s)) << lg_wpr) + w];
-            size_t t = hibase | ((size_t)m << a.L0) | lo;
-            uint32_t *dst = reinterpret_cast<uint32_t *>(a.dst + t * a.S + col) + w;
-            if (a.accumulate) acc ^= *dst;
+        for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
+            const uint32_t m = v >> lg_vpr, c = v & (vpr - 1u);
+            if (c * 16 >= width) continue;
+            uint4 acc = make_uint4(0, 0, 0, 0);
+            for (uint32_t s = 0; s < nlev; s++) {
+                if (!((m >> s) & 1u)) {
+                    const uint4 x = data[((m | (1u << s)) << lg_vpr) + c];
+                    acc.x ^= x.x;
+                    acc.y ^= x.y;
+                    acc.z ^= x.z;
+                    acc.w ^= x.w;
+                }
+            }
+            const size_t t = hibase | ((size_t)m << a.L0) | lo;
+            uint4 *dst = reinterpret_cast<uint4 *>(a.dst + t * a.S + col + c * 16);
+            if (a.accumulate) {
+                const uint4 d = *dst;
+                acc.x ^= d.x;
+                acc.y ^= d.y;
+                acc.z ^= d.z;
+                acc.w ^= d.w;
+            }
             *dst = acc;
         }
     }
@@ -338,9 +392,17 @@ cudaError_t pass_impl(const PassArgs &a, cudaStream_t s)
 {
     const uint32_t nrows = 1u << a.nlev;
     const uint32_t lg_cw = pick_lg_cw(nrows, a.S);
-    const size_t smem = tab_bytes<R>(nrows - 1) + ((size_t)nrows << lg_cw);
-    dim3 grid = pick_grid(a.h >> a.nlev, a.S, lg_cw);
-    k_pass<R, INV><<<grid, kThreads, smem, s>>>(a, lg_cw);
+    const size_t smem = tab_bytes<R>(nrows - 1) + (2 * (size_t)nrows << lg_cw);
+    const uint32_t ngroups = a.h >> a.nlev;
+    const size_t ntiles = (a.S + (1ull << lg_cw) - 1) >> lg_cw;
+    // About 4 tiles per CTA and at least ~6 CTAs per SM in total.
+    size_t y = (ntiles + 3) / 4;
+    const size_t want = (kSms * 6 + ngroups - 1) / ngroups;
+    if (y < want) y = want;
+    if (y > ntiles) y = ntiles;
+    if (y < 1) y = 1;
+    if (y > 65535) y = 65535;
+    k_pass<R, INV><<<dim3(ngroups, (unsigned)y, 1), kPassThreads, smem, s>>>(a, lg_cw);
     return cudaGetLastError();
 }
 
