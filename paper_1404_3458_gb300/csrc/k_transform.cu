@@ -43,53 +43,70 @@ template <> struct TabRef<8> {
     uint32_t b0;
 };
 
-template <int R> __device__ __forceinline__ TabRef<R> tab_ref(uint32_t q, uint32_t nrec);
-template <> __device__ __forceinline__ TabRef<16> tab_ref<16>(uint32_t q, uint32_t nrec)
+// tab: shared-window address of the record regions (128-byte aligned).
+template <int R> __device__ __forceinline__ TabRef<R> tab_ref(uint32_t tab, uint32_t q, uint32_t nrec);
+template <> __device__ __forceinline__ TabRef<16> tab_ref<16>(uint32_t tab, uint32_t q, uint32_t nrec)
 {
-    return {q << 7, (nrec + q) << 7, (nrec << 8) + (q << 5)};
+    return {tab + (q << 7), tab + ((nrec + q) << 7), tab + (nrec << 8) + (q << 5)};
 }
-template <> __device__ __forceinline__ TabRef<8> tab_ref<8>(uint32_t q, uint32_t)
+template <> __device__ __forceinline__ TabRef<8> tab_ref<8>(uint32_t tab, uint32_t q, uint32_t)
 {
-    return {q << 8};
+    return {tab + (q << 8)};
 }
 
-// c * w for the two GF(2^16) elements packed in w; `off` is a compile-time
-// multiple of 128 (resp. 32 for region 2) added to every base.
-template <uint32_t OFF0, uint32_t OFF2>
-__device__ __forceinline__ uint32_t mul16(const uint8_t *tab, uint32_t w, const TabRef<16> &t)
+// Shared-memory loads/stores with 32-bit shared-window addresses and a
+// compile-time immediate offset.
+template <uint32_t OFF> __device__ __forceinline__ uint32_t lds_u16(uint32_t a)
 {
-    const uint32_t t0 = *reinterpret_cast<const uint16_t *>(tab + ((((w << 1) & 0x7Eu) | t.b0) + OFF0));
-    const uint32_t t1 = *reinterpret_cast<const uint16_t *>(tab + ((((w >> 5) & 0x7Eu) | t.b1) + OFF0));
-    const uint32_t t2 = *reinterpret_cast<const uint16_t *>(tab + ((((w >> 11) & 0x1Eu) | t.b2) + OFF2));
-    const uint32_t t3 = *reinterpret_cast<const uint16_t *>(tab + ((((w >> 15) & 0x7Eu) | t.b0) + OFF0));
-    const uint32_t t4 = *reinterpret_cast<const uint16_t *>(tab + ((((w >> 21) & 0x7Eu) | t.b1) + OFF0));
-    const uint32_t t5 = *reinterpret_cast<const uint16_t *>(tab + ((((w >> 27) & 0x1Eu) | t.b2) + OFF2));
+    uint32_t v;
+    asm volatile("ld.shared.u16 %0, [%1+%2];" : "=r"(v) : "r"(a), "n"(OFF));
+    return v;
+}
+template <uint32_t OFF> __device__ __forceinline__ uint32_t lds_u8(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u8 %0, [%1+%2];" : "=r"(v) : "r"(a), "n"(OFF));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts_u32(uint32_t a, uint32_t v) { asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v)); }
+
+// c * w for the two GF(2^16) elements packed in w; the table bases in t are
+// shared-window addresses, OFF0/OFF2 compile-time record offsets.
+template <uint32_t OFF0, uint32_t OFF2>
+__device__ __forceinline__ uint32_t mul16(uint32_t w, const TabRef<16> &t)
+{
+    const uint32_t t0 = lds_u16<OFF0>(((w << 1) & 0x7Eu) | t.b0);
+    const uint32_t t1 = lds_u16<OFF0>(((w >> 5) & 0x7Eu) | t.b1);
+    const uint32_t t2 = lds_u16<OFF2>(((w >> 11) & 0x1Eu) | t.b2);
+    const uint32_t t3 = lds_u16<OFF0>(((w >> 15) & 0x7Eu) | t.b0);
+    const uint32_t t4 = lds_u16<OFF0>(((w >> 21) & 0x7Eu) | t.b1);
+    const uint32_t t5 = lds_u16<OFF2>(((w >> 27) & 0x1Eu) | t.b2);
     return (t0 ^ t1 ^ t2) | ((t3 ^ t4 ^ t5) << 16);
 }
 
 template <uint32_t OFF0>
-__device__ __forceinline__ uint32_t mul8(const uint8_t *tab, uint32_t w, const TabRef<8> &t)
+__device__ __forceinline__ uint32_t mul8(uint32_t w, const TabRef<8> &t)
 {
-    const uint32_t r0 = tab[((w & 0xFFu) | t.b0) + OFF0];
-    const uint32_t r1 = tab[(((w >> 8) & 0xFFu) | t.b0) + OFF0];
-    const uint32_t r2 = tab[(((w >> 16) & 0xFFu) | t.b0) + OFF0];
-    const uint32_t r3 = tab[((w >> 24) | t.b0) + OFF0];
+    const uint32_t r0 = lds_u8<OFF0>((w & 0xFFu) | t.b0);
+    const uint32_t r1 = lds_u8<OFF0>(((w >> 8) & 0xFFu) | t.b0);
+    const uint32_t r2 = lds_u8<OFF0>(((w >> 16) & 0xFFu) | t.b0);
+    const uint32_t r3 = lds_u8<OFF0>((w >> 24) | t.b0);
     return r0 | (r1 << 8) | (r2 << 16) | (r3 << 24);
 }
 
 // Multiply by the record that is `K` records after the one t points to.
 template <int R, uint32_t K> struct MulK;
 template <uint32_t K> struct MulK<16, K> {
-    static __device__ __forceinline__ uint32_t f(const uint8_t *tab, uint32_t w, const TabRef<16> &t)
-    {
-        return mul16<K * 128, K * 32>(tab, w, t);
-    }
+    static __device__ __forceinline__ uint32_t f(uint32_t w, const TabRef<16> &t) { return mul16<K * 128, K * 32>(w, t); }
 };
 template <uint32_t K> struct MulK<8, K> {
-    static __device__ __forceinline__ uint32_t f(const uint8_t *tab, uint32_t w, const TabRef<8> &t)
-    {
-        return mul8<K * 256>(tab, w, t);
-    }
+    static __device__ __forceinline__ uint32_t f(uint32_t w, const TabRef<8> &t) { return mul8<K * 256>(w, t); }
 };
 
 // Butterflies of local level j (0 <= j < Q) on the 2^Q registers x[], whose
@@ -97,7 +114,7 @@ template <uint32_t K> struct MulK<8, K> {
 // (base >> (s0+j+1)) + (u >> (j+1)) of level s0 + j.
 template <int R, int INV, int Q, int J, int U>
 struct LevelStep {
-    static __device__ __forceinline__ void run(uint32_t *x, const uint8_t *tab, const TabRef<R> &t)
+    static __device__ __forceinline__ void run(uint32_t *x, const TabRef<R> &t)
     {
         if constexpr (U < (1 << Q)) {
             if constexpr ((U & (1 << J)) == 0) {
@@ -106,27 +123,27 @@ struct LevelStep {
                 uint32_t &B = x[U | (1 << J)];
                 if constexpr (INV) {
                     B ^= A;
-                    A ^= MulK<R, K>::f(tab, B, t);
+                    A ^= MulK<R, K>::f(B, t);
                 } else {
-                    A ^= MulK<R, K>::f(tab, B, t);
+                    A ^= MulK<R, K>::f(B, t);
                     B ^= A;
                 }
             }
-            LevelStep<R, INV, Q, J, U + 1>::run(x, tab, t);
+            LevelStep<R, INV, Q, J, U + 1>::run(x, t);
         }
     }
 };
 
 template <int R, int INV, int Q, int JJ>
-__device__ __forceinline__ void round_levels(uint32_t *x, const uint8_t *tab, uint32_t nrec, uint32_t nrows,
+__device__ __forceinline__ void round_levels(uint32_t *x, uint32_t tab, uint32_t nrec, uint32_t nrows,
                                              uint32_t base, uint32_t s0)
 {
     if constexpr (JJ < Q) {
         constexpr int J = INV ? JJ : Q - 1 - JJ;
         const uint32_t s = s0 + J;
         const uint32_t q = rec_base(nrows, s) + (base >> (s + 1));
-        const TabRef<R> t = tab_ref<R>(q, nrec);
-        LevelStep<R, INV, Q, J, 0>::run(x, tab, t);
+        const TabRef<R> t = tab_ref<R>(tab, q, nrec);
+        LevelStep<R, INV, Q, J, 0>::run(x, t);
         round_levels<R, INV, Q, JJ + 1>(x, tab, nrec, nrows, base, s0);
     }
 }
@@ -134,28 +151,28 @@ __device__ __forceinline__ void round_levels(uint32_t *x, const uint8_t *tab, ui
 // One round: every thread takes 2^Q rows (bits s0 .. s0+Q-1 free) of one
 // column word, runs Q levels in registers and writes the rows back.
 template <int R, int INV, int Q>
-__device__ __forceinline__ void round_q(uint32_t *data, const uint8_t *tab, uint32_t nrec, uint32_t nrows,
-                                        uint32_t lg_w, uint32_t s0)
+__device__ __forceinline__ void round_q(uint32_t data, uint32_t tab, uint32_t nrec, uint32_t nrows, uint32_t lg_w,
+                                        uint32_t s0)
 {
     const uint32_t W = 1u << lg_w;
     const uint32_t items = (nrows >> Q) << lg_w;
-    const uint32_t stride = 1u << (s0 + lg_w);
+    const uint32_t stride = 4u << (s0 + lg_w); // bytes between the rows of a group
     for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
         const uint32_t g = it >> lg_w, w = it & (W - 1u);
         const uint32_t base = ((g >> s0) << (s0 + Q)) | (g & ((1u << s0) - 1u));
-        uint32_t *p = data + (base << lg_w) + w;
+        const uint32_t p = data + (((base << lg_w) + w) << 2);
         uint32_t x[1 << Q];
 #pragma unroll
-        for (int u = 0; u < (1 << Q); u++) x[u] = p[u * stride];
+        for (int u = 0; u < (1 << Q); u++) x[u] = lds_u32(p + u * stride);
         round_levels<R, INV, Q, 0>(x, tab, nrec, nrows, base, s0);
 #pragma unroll
-        for (int u = 0; u < (1 << Q); u++) p[u * stride] = x[u];
+        for (int u = 0; u < (1 << Q); u++) sts_u32(p + u * stride, x[u]);
     }
 }
 
 template <int R, int INV>
-__device__ __forceinline__ void run_round(uint32_t q, uint32_t *data, const uint8_t *tab, uint32_t nrec,
-                                          uint32_t nrows, uint32_t lg_w, uint32_t s0)
+__device__ __forceinline__ void run_round(uint32_t q, uint32_t data, uint32_t tab, uint32_t nrec, uint32_t nrows,
+                                          uint32_t lg_w, uint32_t s0)
 {
     switch (q) {
     case 1: round_q<R, INV, 1>(data, tab, nrec, nrows, lg_w, s0); break;
@@ -201,6 +218,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(PassArgs a, uint32_t l
     extern __shared__ __align__(128) uint8_t sm[];
     const uint32_t nlev = a.nlev, nrows = 1u << nlev, nrec = nrows - 1;
     uint8_t *tab = sm;
+    const uint32_t stab = (uint32_t)__cvta_generic_to_shared(sm);
     const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
     uint8_t *const buf0 = sm + tab_bytes<R>(nrec);
     const uint32_t tile_bytes = nrows << lg_cw;
@@ -251,20 +269,21 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(PassArgs a, uint32_t l
     const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, qb = nlev - qa;
     for (uint32_t t = 0; t < ntiles; t++) {
         uint32_t *data = reinterpret_cast<uint32_t *>(buf0 + (t & 1u) * tile_bytes);
+        const uint32_t sdata = (uint32_t)__cvta_generic_to_shared(data);
         cp_async_wait1(); // tile t (and the records) have landed for this thread
         __syncthreads();
         if (INV) {
-            run_round<R, INV>(qa, data, tab, nrec, nrows, lg_w, 0);
+            run_round<R, INV>(qa, sdata, stab, nrec, nrows, lg_w, 0);
             if (qb) {
                 __syncthreads();
-                run_round<R, INV>(qb, data, tab, nrec, nrows, lg_w, qa);
+                run_round<R, INV>(qb, sdata, stab, nrec, nrows, lg_w, qa);
             }
         } else {
             if (qb) {
-                run_round<R, INV>(qb, data, tab, nrec, nrows, lg_w, qa);
+                run_round<R, INV>(qb, sdata, stab, nrec, nrows, lg_w, qa);
                 __syncthreads();
             }
-            run_round<R, INV>(qa, data, tab, nrec, nrows, lg_w, 0);
+            run_round<R, INV>(qa, sdata, stab, nrec, nrows, lg_w, 0);
         }
         __syncthreads();
         {
