@@ -148,13 +148,17 @@ LCH_API uint64_t lch_launch_count(const lch_ctx *ctx);
 
 /* Diagnostics.  With profiling on, every kernel launch is bracketed by CUDA
  * events recorded on its own stream; lch_profile_read() returns, per kind,
- * the number of launches, their summed device time in milliseconds and the
+ * the number of launches, their summed device time in milliseconds, the
  * algorithmic bytes they moved (each launch counts the rows it must read and
  * write once: 2 x rows x shard_bytes, plus rows x shard_bytes when it also
- * reads its output).  Enabling (or re-enabling) clears the counters.
- * Reading synchronises on the recorded events. */
+ * reads its output) and the algorithmic field multiplications they performed
+ * (a transform pass over levels [L0, L0+q) of an h-point transform counts
+ * (h/2) q per column, Sec. III.D; a row scaling counts one per element).
+ * Enabling (or re-enabling) clears the counters.  Reading synchronises on the
+ * recorded events. */
 LCH_API int lch_profile_enable(lch_ctx *ctx, int on);
-LCH_API int lch_profile_read(lch_ctx *ctx, int kind, uint64_t *launches, double *total_ms, uint64_t *bytes);
+LCH_API int lch_profile_read(lch_ctx *ctx, int kind, uint64_t *launches, double *total_ms, uint64_t *bytes,
+                             uint64_t *mults);
 
 #ifdef __cplusplus
 }

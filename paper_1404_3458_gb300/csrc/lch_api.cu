@@ -23,7 +23,7 @@ struct lch_ctx {
     struct Rec {
         cudaEvent_t a, b;
         int kind;
-        uint64_t bytes;
+        uint64_t bytes, mults;
     };
     bool prof_on = false;
     std::vector<Rec> prof;
@@ -158,21 +158,23 @@ lch_ctx::Rec *prof_begin(lch_ctx *ctx, cudaStream_t s)
     return r;
 }
 
-void prof_end(lch_ctx::Rec *r, cudaStream_t s, int kind, uint64_t bytes)
+void prof_end(lch_ctx::Rec *r, cudaStream_t s, int kind, uint64_t bytes, uint64_t mults)
 {
     if (!r) return;
     r->kind = kind;
     r->bytes = bytes;
+    r->mults = mults;
     cudaEventRecord(r->b, s);
 }
 
-#define PROF(kind, bytes, call)                                                                    \
+#define PROFM(kind, bytes, mults, call)                                                            \
     do {                                                                                           \
         lch_ctx::Rec *pr_ = prof_begin(ctx, s);                                                    \
         cudaError_t e_ = (call);                                                                   \
-        prof_end(pr_, s, kind, bytes);                                                             \
+        prof_end(pr_, s, kind, bytes, mults);                                                      \
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);                                       \
     } while (0)
+#define PROF(kind, bytes, call) PROFM(kind, bytes, 0, call)
 
 // Levels [0, lgh) are split into at most two passes of <= 8 levels each.
 void split_levels(uint32_t lgh, uint32_t *a, uint32_t *b)
@@ -211,16 +213,17 @@ int transform(lch_ctx *ctx, int field, uint32_t h, uint32_t l, int inverse, cons
         first_n = a;
     }
     const uint64_t bytes = 2ull * h * S;
+    const uint64_t cols = S / (field / 8), per_level = (uint64_t)(h / 2) * cols;
     p.src = src;
     p.dst = dst;
     p.L0 = first_L0;
     p.nlev = first_n;
-    PROF(LCH_KIND_PASS, bytes, launch_pass(field, p, s, &ctx->launches));
+    PROFM(LCH_KIND_PASS, bytes, per_level * first_n, launch_pass(field, p, s, &ctx->launches));
     if (b) {
         p.src = dst;
         p.L0 = second_L0;
         p.nlev = second_n;
-        PROF(LCH_KIND_PASS, bytes, launch_pass(field, p, s, &ctx->launches));
+        PROFM(LCH_KIND_PASS, bytes, per_level * second_n, launch_pass(field, p, s, &ctx->launches));
     }
     return LCH_OK;
 }
@@ -235,7 +238,8 @@ int derivative(lch_ctx *ctx, int field, uint32_t h, uint8_t *src, uint8_t *dst, 
         return LCH_OK;
     }
     // d^d_i = d_i B_i (eq. dimathrmd)
-    PROF(LCH_KIND_ROWSCALE, 2ull * h * S, launch_rowscale(field, src, src, S, h, t.B, 0, s, &ctx->launches));
+    const uint64_t elems = (uint64_t)h * (S / (field / 8));
+    PROFM(LCH_KIND_ROWSCALE, 2ull * h * S, elems, launch_rowscale(field, src, src, S, h, t.B, 0, s, &ctx->launches));
     uint32_t a, b;
     split_levels(lgh, &a, &b);
     SupersetArgs q;
@@ -254,7 +258,7 @@ int derivative(lch_ctx *ctx, int field, uint32_t h, uint8_t *src, uint8_t *dst, 
         PROF(LCH_KIND_DERIV, 3ull * h * S, launch_superset(q, s, &ctx->launches));
     }
     // divide coefficient j by B_j (eq. XDhx3)
-    PROF(LCH_KIND_ROWSCALE, 2ull * h * S, launch_rowscale(field, dst, dst, S, h, t.Binv, 0, s, &ctx->launches));
+    PROFM(LCH_KIND_ROWSCALE, 2ull * h * S, elems, launch_rowscale(field, dst, dst, S, h, t.Binv, 0, s, &ctx->launches));
     return LCH_OK;
 }
 
@@ -290,8 +294,9 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
     // Step 1: Pi(j) off E and 1/Pi'(j) on E.
     PROF(LCH_KIND_LOCATOR, 0, launch_locator(field, t, lgn, bits, ctx->fl[field == LCH_GF16][lgn], work, pre, post, s, &ctx->launches));
     // Step 2: Phi = F * Pi, zero on erased rows (eq. hatF(l)).
-    PROF(LCH_KIND_ROWSCALE, (uint64_t)(n - ne) * S + (uint64_t)n * S,
-         launch_rowscale(field, phi, shards, S, n, pre, 0, s, &ctx->launches));
+    const uint64_t cols = S / (field / 8);
+    PROFM(LCH_KIND_ROWSCALE, (uint64_t)(n - ne) * S + (uint64_t)n * S, (uint64_t)(n - ne) * cols,
+          launch_rowscale(field, phi, shards, S, n, pre, 0, s, &ctx->launches));
     // Step 3: coefficients of hatF.
     rc = transform(ctx, field, n, 0, 1, phi, phi, S, s);
     if (rc) return rc;
@@ -302,7 +307,8 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
     rc = transform(ctx, field, n, 0, 0, phi2, phi2, S, s);
     if (rc) return rc;
     // Step 6: F(j) = hatF'(j) / Pi'(j), written to the erased rows only.
-    PROF(LCH_KIND_ROWSCALE, 2ull * ne * S, launch_rowscale(field, shards, phi2, S, n, post, 1, s, &ctx->launches));
+    PROFM(LCH_KIND_ROWSCALE, 2ull * ne * S, (uint64_t)ne * cols,
+          launch_rowscale(field, shards, phi2, S, n, post, 1, s, &ctx->launches));
     return LCH_OK;
 }
 
@@ -478,12 +484,13 @@ LCH_API int lch_profile_enable(lch_ctx *ctx, int on)
     return LCH_OK;
 }
 
-LCH_API int lch_profile_read(lch_ctx *ctx, int kind, uint64_t *launches, double *total_ms, uint64_t *bytes)
+LCH_API int lch_profile_read(lch_ctx *ctx, int kind, uint64_t *launches, double *total_ms, uint64_t *bytes,
+                             uint64_t *mults)
 {
-    if (!ctx || !launches || !total_ms || !bytes) return fail(LCH_EINVAL, "NULL argument");
+    if (!ctx || !launches || !total_ms || !bytes || !mults) return fail(LCH_EINVAL, "NULL argument");
     if (kind < 0 || kind >= LCH_KIND_COUNT) return fail(LCH_EINVAL, "unknown kernel kind %d", kind);
     DeviceScope ds(ctx->device);
-    uint64_t n = 0, by = 0;
+    uint64_t n = 0, by = 0, mu = 0;
     double ms = 0;
     for (size_t i = 0; i < ctx->prof_used; i++) {
         const lch_ctx::Rec &r = ctx->prof[i];
@@ -494,10 +501,12 @@ LCH_API int lch_profile_read(lch_ctx *ctx, int kind, uint64_t *launches, double 
         n++;
         ms += t;
         by += r.bytes;
+        mu += r.mults;
     }
     *launches = n;
     *total_ms = ms;
     *bytes = by;
+    *mults = mu;
     return LCH_OK;
 }
 

@@ -60,7 +60,7 @@ def load() -> ctypes.CDLL:
         "lch_derivative_noalloc": (i, [i, u32, vp, sz, vp]),
         "lch_profile_enable": (i, [vp, i]),
         "lch_profile_read": (i, [vp, i, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
-                                 ctypes.POINTER(ctypes.c_uint64)]),
+                                 ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -136,11 +136,13 @@ class Context:
         _check(load().lch_profile_enable(self._h, int(on)))
 
     def profile(self, kind: int) -> dict:
-        """Launches, summed device ms and algorithmic bytes of one kernel kind
-        since profiling was enabled (see lch_profile_read)."""
-        n, ms, by = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_uint64()
-        _check(load().lch_profile_read(self._h, kind, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
-        return {"launches": int(n.value), "ms": float(ms.value), "bytes": int(by.value)}
+        """Launches, summed device ms, algorithmic bytes and field
+        multiplications of one kernel kind since profiling was enabled (see
+        lch_profile_read)."""
+        n, ms, by, mu = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().lch_profile_read(self._h, kind, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by),
+                                       ctypes.byref(mu)))
+        return {"launches": int(n.value), "ms": float(ms.value), "bytes": int(by.value), "mults": int(mu.value)}
 
     # Sec. III: Psi_h^l and its inverse, in place on h rows.
     def fft(self, field: int, l: int, buf, stream=None):
