@@ -353,6 +353,218 @@ __global__ void __launch_bounds__(kThreads) k_superset(SupersetArgs a, uint32_t 
     }
 }
 
+// ---------------------------------------------------------------- derivative
+// Fused formal derivative over one bit group (Sec. IV.B): with u = B (.) x,
+//   MODE 0: dst = S(u)                   (first of two bit groups)
+//   MODE 1: dst = B^-1 (.) (S(u) ^ xin)  (second group; xin = the first's S)
+//   MODE 2: dst = B^-1 (.) S(u)          (all bits in one tile)
+// where S(u)_j = XOR over the group's bits l with bit l of j clear of
+// u_{j + 2^l} (eq. XDhx3).  The per-row constants B_j, B_j^-1 use nibble
+// records; a CTA keeps its row group's records in shared memory while it
+// walks its column tiles (cp.async double buffered).
+
+template <int R> struct NibRef;
+template <> struct NibRef<16> {
+    uint32_t b0, b1, b2, b3;
+};
+template <> struct NibRef<8> {
+    uint32_t b0, b1;
+};
+// Sub-table k of record q lives at region + (k * nrec + q) * sub_bytes.
+template <int R> __device__ __forceinline__ NibRef<R> nib_ref(uint32_t region, uint32_t q, uint32_t nrec);
+template <> __device__ __forceinline__ NibRef<16> nib_ref<16>(uint32_t region, uint32_t q, uint32_t nrec)
+{
+    const uint32_t b = region + (q << 5);
+    return {b, b + (nrec << 5), b + (nrec << 6), b + nrec * 96u};
+}
+template <> __device__ __forceinline__ NibRef<8> nib_ref<8>(uint32_t region, uint32_t q, uint32_t nrec)
+{
+    const uint32_t b = region + (q << 4);
+    return {b, b + (nrec << 4)};
+}
+
+template <int R> __device__ __forceinline__ uint32_t mul_nib(uint32_t w, const NibRef<R> &t);
+template <> __device__ __forceinline__ uint32_t mul_nib<16>(uint32_t w, const NibRef<16> &t)
+{
+    const uint32_t lo = lds_u16<0>(((w << 1) & 0x1Eu) | t.b0) ^ lds_u16<0>(((w >> 3) & 0x1Eu) | t.b1) ^
+                        lds_u16<0>(((w >> 7) & 0x1Eu) | t.b2) ^ lds_u16<0>(((w >> 11) & 0x1Eu) | t.b3);
+    const uint32_t hi = lds_u16<0>(((w >> 15) & 0x1Eu) | t.b0) ^ lds_u16<0>(((w >> 19) & 0x1Eu) | t.b1) ^
+                        lds_u16<0>(((w >> 23) & 0x1Eu) | t.b2) ^ lds_u16<0>(((w >> 27) & 0x1Eu) | t.b3);
+    return lo | (hi << 16);
+}
+template <> __device__ __forceinline__ uint32_t mul_nib<8>(uint32_t w, const NibRef<8> &t)
+{
+    uint32_t r = 0;
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+        const uint32_t v = lds_u8<0>(((w >> (8 * b)) & 0xFu) | t.b0) ^ lds_u8<0>(((w >> (8 * b + 4)) & 0xFu) | t.b1);
+        r |= v << (8 * b);
+    }
+    return r;
+}
+
+// Neighbour sums inside one register group of 2^Q rows (bits s0 .. s0+Q-1 of
+// the tile-local row index): acc[u] ^= x[u | 2^b] for every b < Q with bit b
+// of u clear.
+template <int Q, int U, int B> struct NbrSum {
+    static __device__ __forceinline__ void run(const uint32_t *x, uint32_t *acc)
+    {
+        if constexpr (U < (1 << Q)) {
+            if constexpr (B < Q) {
+                if constexpr ((U & (1 << B)) == 0) acc[U] ^= x[U | (1 << B)];
+                NbrSum<Q, U, B + 1>::run(x, acc);
+            } else {
+                NbrSum<Q, U + 1, 0>::run(x, acc);
+            }
+        }
+    }
+};
+
+// Round over bits [s0, s0+Q) of a tile.  FIRST: acc = S_round(u) (^ the
+// acc tile when it already holds xin) -> acc tile.  LAST: out = B^-1? (acc
+// tile ^ S_round(u)) -> global.  A round can be both (single-round tiles).
+template <int R, int Q, bool FIRST, bool LAST, bool INV>
+__device__ __forceinline__ void deriv_round(const DerivArgs &a, uint32_t su, uint32_t sacc, bool acc_has_data,
+                                            uint32_t s_binv, uint32_t nrows, uint32_t lg_w, uint32_t s0,
+                                            uint32_t hibase, uint32_t lo, size_t col, uint32_t width)
+{
+    const uint32_t W = 1u << lg_w;
+    const uint32_t items = (nrows >> Q) << lg_w;
+    const uint32_t stride = 4u << (s0 + lg_w);
+    for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
+        const uint32_t g = it >> lg_w, w = it & (W - 1u);
+        const uint32_t base = ((g >> s0) << (s0 + Q)) | (g & ((1u << s0) - 1u));
+        const uint32_t off = ((base << lg_w) + w) << 2;
+        uint32_t x[1 << Q], acc[1 << Q];
+#pragma unroll
+        for (int u = 0; u < (1 << Q); u++) x[u] = lds_u32(su + off + u * stride);
+#pragma unroll
+        for (int u = 0; u < (1 << Q); u++) acc[u] = (!FIRST || acc_has_data) ? lds_u32(sacc + off + u * stride) : 0u;
+        NbrSum<Q, 0, 0>::run(x, acc);
+        if constexpr (!LAST) {
+#pragma unroll
+            for (int u = 0; u < (1 << Q); u++) sts_u32(sacc + off + u * stride, acc[u]);
+        } else {
+            if (w * 4 < width) {
+                const size_t row0 = hibase | ((size_t)base << a.L0) | lo;
+                uint8_t *p = a.dst + row0 * a.S + col + w * 4;
+                const size_t rstep = a.S << (s0 + a.L0);
+#pragma unroll
+                for (int u = 0; u < (1 << Q); u++) {
+                    uint32_t v = acc[u];
+                    if constexpr (INV) v = mul_nib<R>(v, nib_ref<R>(s_binv, base | ((uint32_t)u << s0), nrows));
+                    *reinterpret_cast<uint32_t *>(p + u * rstep) = v;
+                }
+            }
+        }
+    }
+}
+
+template <int R, bool FIRST, bool LAST, bool INV>
+__device__ __forceinline__ void deriv_round_q(uint32_t q, const DerivArgs &a, uint32_t su, uint32_t sacc,
+                                              bool acc_has_data, uint32_t s_binv, uint32_t nrows, uint32_t lg_w,
+                                              uint32_t s0, uint32_t hibase, uint32_t lo, size_t col, uint32_t width)
+{
+    switch (q) {
+    case 1: deriv_round<R, 1, FIRST, LAST, INV>(a, su, sacc, acc_has_data, s_binv, nrows, lg_w, s0, hibase, lo, col, width); break;
+    case 2: deriv_round<R, 2, FIRST, LAST, INV>(a, su, sacc, acc_has_data, s_binv, nrows, lg_w, s0, hibase, lo, col, width); break;
+    case 3: deriv_round<R, 3, FIRST, LAST, INV>(a, su, sacc, acc_has_data, s_binv, nrows, lg_w, s0, hibase, lo, col, width); break;
+    default: deriv_round<R, 4, FIRST, LAST, INV>(a, su, sacc, acc_has_data, s_binv, nrows, lg_w, s0, hibase, lo, col, width); break;
+    }
+}
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(kPassThreads, 1) k_deriv(DerivArgs a, uint32_t lg_cw)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
+    constexpr bool kX = MODE == 1, kInv = MODE != 0;
+    const uint32_t nlev = a.nlev, nrows = 1u << nlev;
+    const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
+    const uint32_t rec_bytes = nrows * NibRec<R>::bytes;
+    const uint32_t s_brec = (uint32_t)__cvta_generic_to_shared(sm);
+    const uint32_t s_binv = s_brec + rec_bytes;
+    uint8_t *stage0 = sm + (kInv ? 2 : 1) * rec_bytes;
+    const uint32_t tile_bytes = nrows << lg_cw;
+    const uint32_t stage_bytes = 2 * tile_bytes; // u tile + accumulator tile
+    const uint32_t g = blockIdx.x;
+    const uint32_t lo = g & ((1u << a.L0) - 1u);
+    const uint32_t hibase = (g >> a.L0) << (a.L0 + nlev);
+    const size_t col_step = (size_t)gridDim.y << lg_cw;
+    const size_t col0 = (size_t)blockIdx.y << lg_cw;
+    const uint32_t ntiles = col0 < a.S ? (uint32_t)((a.S - col0 + col_step - 1) / col_step) : 0;
+
+    // Records of the tile rows, laid out by sub-table (see nib_ref).
+    constexpr uint32_t cpr = NibRec<R>::bytes / 16, cps = NibRec<R>::sub_bytes / 16;
+    for (uint32_t v = threadIdx.x; v < nrows * cpr * (kInv ? 2 : 1); v += blockDim.x) {
+        const uint32_t which = v / (nrows * cpr), vv = v - which * nrows * cpr;
+        const uint32_t q = vv / cpr, c = vv - q * cpr;
+        const uint32_t k = c / cps, part = c - k * cps;
+        const size_t row = hibase | ((size_t)q << a.L0) | lo;
+        const uint8_t *src = (which ? a.binvnib : a.bnib) + row * NibRec<R>::bytes + c * 16;
+        cp_async16(sm + which * rec_bytes + (k * nrows + q) * NibRec<R>::sub_bytes + part * 16, src);
+    }
+
+    auto issue = [&](uint32_t t, uint8_t *dstbuf) {
+        const size_t col = col0 + (size_t)t * col_step;
+        const size_t rem = a.S - col;
+        const uint32_t width = rem < cw ? (uint32_t)rem : cw;
+        for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
+            const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
+            if (c * 16 < width) {
+                const size_t off = (hibase | ((size_t)m << a.L0) | lo) * a.S + col + c * 16;
+                cp_async16(dstbuf + v * 16, a.src + off);
+                if (kX) cp_async16(dstbuf + tile_bytes + v * 16, a.xin + off);
+            }
+        }
+    };
+    if (ntiles > 0) issue(0, stage0);
+    cp_async_commit();
+    if (ntiles > 1) issue(1, stage0 + stage_bytes);
+    cp_async_commit();
+
+    const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, qb = nlev - qa;
+    for (uint32_t t = 0; t < ntiles; t++) {
+        uint8_t *stage = stage0 + (t & 1u) * stage_bytes;
+        const uint32_t su = (uint32_t)__cvta_generic_to_shared(stage), sacc = su + tile_bytes;
+        const size_t col = col0 + (size_t)t * col_step;
+        const size_t rem = a.S - col;
+        const uint32_t width = rem < cw ? (uint32_t)rem : cw;
+        cp_async_wait1();
+        __syncthreads();
+        // u = B (.) x, in place; 8 independent words per thread for ILP.
+        const uint32_t items = nrows << lg_w;
+        for (uint32_t it0 = threadIdx.x; it0 < items; it0 += 8 * blockDim.x) {
+            uint32_t x[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const uint32_t it = it0 + j * blockDim.x;
+                x[j] = it < items ? lds_u32(su + (it << 2)) : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const uint32_t it = it0 + j * blockDim.x;
+                if (it < items) x[j] = mul_nib<R>(x[j], nib_ref<R>(s_brec, it >> lg_w, nrows));
+            }
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const uint32_t it = it0 + j * blockDim.x;
+                if (it < items) sts_u32(su + (it << 2), x[j]);
+            }
+        }
+        __syncthreads();
+        if (qb == 0) {
+            deriv_round_q<R, true, true, kInv>(qa, a, su, sacc, kX, s_binv, nrows, lg_w, 0, hibase, lo, col, width);
+        } else {
+            deriv_round_q<R, true, false, kInv>(qa, a, su, sacc, kX, s_binv, nrows, lg_w, 0, hibase, lo, col, width);
+            __syncthreads();
+            deriv_round_q<R, false, true, kInv>(qb, a, su, sacc, true, s_binv, nrows, lg_w, qa, hibase, lo, col, width);
+        }
+        __syncthreads();
+        if (t + 2 < ntiles) issue(t + 2, stage);
+        cp_async_commit();
+    }
+}
+
 template <int R>
 __global__ void __launch_bounds__(kThreads)
     k_rowscale(uint8_t *dst, const uint8_t *src, size_t S, const uint16_t *__restrict__ coef, int skip_zero)
@@ -360,7 +572,12 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ __align__(16) uint8_t T[FT<R>::rec_bytes];
     const uint32_t row = blockIdx.x;
     const uint32_t c = coef[row];
-    if (skip_zero && c == 0) return;
+    if (c == 0) { // erased row of Phi: zero it without reading it
+        if (skip_zero) return;
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst + (size_t)row * S);
+        for (size_t v = threadIdx.x; v < S / 16; v += blockDim.x) d4[v] = make_uint4(0, 0, 0, 0);
+        return;
+    }
     for (uint32_t idx = threadIdx.x; idx < FT<R>::rec_entries; idx += blockDim.x)
         rec_store<R>(T, idx, rec_entry<R>(c, idx));
     __syncthreads();
@@ -429,12 +646,18 @@ cudaError_t pass_impl(const PassArgs &a, cudaStream_t s)
 
 cudaError_t configure_transform_kernels()
 {
-    const int big = 200 * 1024;
+    const int big = 220 * 1024;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_pass<8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_pass<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_pass<16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_pass<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_deriv<8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_deriv<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_deriv<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_deriv<16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_deriv<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_deriv<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     return cudaFuncSetAttribute(k_superset, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
@@ -454,6 +677,32 @@ cudaError_t launch_superset(const SupersetArgs &a, cudaStream_t s, uint64_t *lau
     k_superset<<<grid, kThreads, smem, s>>>(a, lg_cw);
     *launches += 1;
     return cudaGetLastError();
+}
+
+template <int R, int MODE>
+cudaError_t deriv_impl(const DerivArgs &a, cudaStream_t s)
+{
+    const uint32_t nrows = 1u << a.nlev;
+    const uint32_t lg_cw = pick_lg_cw(nrows, a.S);
+    const size_t rec = (size_t)nrows * NibRec<R>::bytes * (MODE == 0 ? 1 : 2);
+    const size_t smem = rec + 2 * 2 * ((size_t)nrows << lg_cw);
+    const uint32_t ngroups = a.h >> a.nlev;
+    const size_t ntiles = (a.S + (1ull << lg_cw) - 1) >> lg_cw;
+    size_t y = (ntiles + 7) / 8;
+    const size_t want = (kSms * 6 + ngroups - 1) / ngroups;
+    if (y < want) y = want;
+    if (y > ntiles) y = ntiles;
+    if (y < 1) y = 1;
+    if (y > 65535) y = 65535;
+    k_deriv<R, MODE><<<dim3(ngroups, (unsigned)y, 1), kPassThreads, smem, s>>>(a, lg_cw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deriv(int r, int mode, const DerivArgs &a, cudaStream_t s, uint64_t *launches)
+{
+    *launches += 1;
+    if (r == 8) return mode == 0 ? deriv_impl<8, 0>(a, s) : mode == 1 ? deriv_impl<8, 1>(a, s) : deriv_impl<8, 2>(a, s);
+    return mode == 0 ? deriv_impl<16, 0>(a, s) : mode == 1 ? deriv_impl<16, 1>(a, s) : deriv_impl<16, 2>(a, s);
 }
 
 cudaError_t launch_rowscale(int r, uint8_t *dst, const uint8_t *src, size_t S, uint32_t rows,

@@ -228,37 +228,32 @@ int transform(lch_ctx *ctx, int field, uint32_t h, uint32_t l, int inverse, cons
     return LCH_OK;
 }
 
-// dst = [src]' (coefficient vectors of h rows); src is scaled in place.
-int derivative(lch_ctx *ctx, int field, uint32_t h, uint8_t *src, uint8_t *dst, size_t S, cudaStream_t s)
+// dst = [src]' (coefficient vectors of h rows): u = B (.) src, neighbour sums
+// split by bit group, B^-1 (.) (Sec. IV.B).  dst may equal src.
+int derivative(lch_ctx *ctx, int field, uint32_t h, const uint8_t *src, uint8_t *dst, uint8_t *tmp, size_t S,
+               cudaStream_t s)
 {
     const FieldTables &t = ctx->tab[field == LCH_GF16];
     const uint32_t lgh = lg2(h);
-    if (lgh == 0) {
+    if (lgh == 0) { // a constant has derivative zero
         CU(cudaMemsetAsync(dst, 0, S, s), "memset");
         return LCH_OK;
     }
-    // d^d_i = d_i B_i (eq. dimathrmd)
-    const uint64_t elems = (uint64_t)h * (S / (field / 8));
-    PROFM(LCH_KIND_ROWSCALE, 2ull * h * S, elems, launch_rowscale(field, src, src, S, h, t.B, 0, s, &ctx->launches));
     uint32_t a, b;
     split_levels(lgh, &a, &b);
-    SupersetArgs q;
-    q.src = src;
-    q.dst = dst;
-    q.S = S;
-    q.h = h;
-    q.L0 = 0;
-    q.nlev = a;
-    q.accumulate = 0;
-    PROF(LCH_KIND_DERIV, 2ull * h * S, launch_superset(q, s, &ctx->launches));
-    if (b) {
-        q.L0 = a;
-        q.nlev = b;
-        q.accumulate = 1;
-        PROF(LCH_KIND_DERIV, 3ull * h * S, launch_superset(q, s, &ctx->launches));
+    const uint64_t elems = (uint64_t)h * (S / (field / 8));
+    DerivArgs d{src, nullptr, dst, S, h, 0, a, t.bnib, t.binvnib};
+    if (b == 0) {
+        PROFM(LCH_KIND_DERIV, 2ull * h * S, 2 * elems, launch_deriv(field, 2, d, s, &ctx->launches));
+        return LCH_OK;
     }
-    // divide coefficient j by B_j (eq. XDhx3)
-    PROFM(LCH_KIND_ROWSCALE, 2ull * h * S, elems, launch_rowscale(field, dst, dst, S, h, t.Binv, 0, s, &ctx->launches));
+    d.dst = tmp; // S_low(u)
+    PROFM(LCH_KIND_DERIV, 2ull * h * S, elems, launch_deriv(field, 0, d, s, &ctx->launches));
+    d.xin = tmp;
+    d.dst = dst;
+    d.L0 = a;
+    d.nlev = b;
+    PROFM(LCH_KIND_DERIV, 3ull * h * S, 2 * elems, launch_deriv(field, 1, d, s, &ctx->launches));
     return LCH_OK;
 }
 
@@ -301,7 +296,7 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
     rc = transform(ctx, field, n, 0, 1, phi, phi, S, s);
     if (rc) return rc;
     // Step 4: formal derivative.
-    rc = derivative(ctx, field, n, phi, phi2, S, s);
+    rc = derivative(ctx, field, n, phi, phi2, phi2, S, s);
     if (rc) return rc;
     // Step 5: evaluate hatF'.
     rc = transform(ctx, field, n, 0, 0, phi2, phi2, S, s);
@@ -378,6 +373,8 @@ LCH_API void lch_ctx_destroy(lch_ctx *ctx)
             cudaFree(t.Binv);
             cudaFree(t.expt);
             cudaFree(t.logt);
+            cudaFree(t.bnib);
+            cudaFree(t.binvnib);
         }
         for (auto &row : ctx->fl)
             for (auto *p : row) cudaFree(p);
@@ -429,9 +426,7 @@ LCH_API int lch_derivative(lch_ctx *ctx, int field, uint32_t h, void *buf, size_
     if ((rc = ensure_tables(ctx, field, s))) return rc;
     if ((rc = ensure_scratch(ctx, (size_t)h * shard_bytes))) return rc;
     uint8_t *p = (uint8_t *)buf;
-    if ((rc = derivative(ctx, field, h, p, ctx->scratch, shard_bytes, s))) return rc;
-    CU(cudaMemcpyAsync(p, ctx->scratch, (size_t)h * shard_bytes, cudaMemcpyDeviceToDevice, s), "copy back");
-    return LCH_OK;
+    return derivative(ctx, field, h, p, p, ctx->scratch, shard_bytes, s);
 }
 
 LCH_API int rs_encode(lch_ctx *ctx, uint32_t n, uint32_t k, int field, void *shards, size_t shard_bytes, void *stream)

@@ -96,6 +96,19 @@ template <> __device__ __forceinline__ uint32_t mul_word<16>(uint32_t w, const u
     return lo | (hi << 16);
 }
 
+// "Nibble" record of a constant c: r/4 sub-tables of 16 entries, sub-table k
+// holding c * (e << 4k).  Smaller than a split-table record (4 lookups per
+// GF(2^16) element instead of 3), used for per-row constants.
+template <int R> struct NibRec {
+    static constexpr uint32_t subs = R / 4;
+    static constexpr uint32_t sub_bytes = 16 * (R / 8);
+    static constexpr uint32_t bytes = subs * sub_bytes; // 128 (GF(2^16)) or 32 (GF(2^8))
+};
+template <int R> __device__ __forceinline__ uint32_t nib_entry(uint32_t c, uint32_t idx)
+{
+    return gf_mul_slow<R>(c, (idx & 15u) << (4 * (idx >> 4)));
+}
+
 // Offset of level i in the per-level factor arrays: level i holds 2^(r-i)
 // entries, one per value of (x >> i), x in [0, 2^r).
 __host__ __device__ __forceinline__ uint32_t level_off(int r, int i)
@@ -114,6 +127,8 @@ struct FieldTables {
     uint16_t *Binv = nullptr; // B_j^-1
     uint16_t *expt = nullptr; // alpha^i, i < 2^r - 1
     uint16_t *logt = nullptr; // log_alpha(x), x != 0; logt[0] = 0
+    uint8_t *bnib = nullptr;  // nibble record of B_j, j < 2^r (NibRec<r>::bytes each)
+    uint8_t *binvnib = nullptr; // nibble record of B_j^-1
     uint32_t wbase[16] = {};  // W_i(w_{2^i}) (host copy, for tests/diagnostics)
 };
 
@@ -157,6 +172,21 @@ struct SupersetArgs {
     int accumulate;
 };
 cudaError_t launch_superset(const SupersetArgs &a, cudaStream_t s, uint64_t *launches);
+
+// Fused derivative over one bit group: see k_deriv.  mode 0: dst = S(B x);
+// mode 1: dst = B^-1 (S(B x) ^ xin); mode 2: dst = B^-1 S(B x).
+struct DerivArgs {
+    const uint8_t *src;
+    const uint8_t *xin;
+    uint8_t *dst;
+    size_t S;
+    uint32_t h;
+    uint32_t L0;
+    uint32_t nlev;
+    const uint8_t *bnib;
+    const uint8_t *binvnib;
+};
+cudaError_t launch_deriv(int r, int mode, const DerivArgs &a, cudaStream_t s, uint64_t *launches);
 
 // dst[t] = src[t] * coef[t] for t < rows (a zero coefficient zeroes the row);
 // with skip_zero, rows whose coefficient is zero are left untouched.
