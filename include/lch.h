@@ -130,6 +130,55 @@ LCH_API int rs_encode(lch_ctx *ctx, uint32_t n, uint32_t k, int field, void *sha
 LCH_API int rs_decode(lch_ctx *ctx, uint32_t n, uint32_t k, int field, void *shards, size_t shard_bytes,
                       const uint8_t *erasure_mask, void *stream);
 
+/* ---- Batches: many independent codewords in one persistent launch -------
+ * (Beyond the paper, which treats one codeword at a time: every stage of
+ * Algorithms 1 and 2 is the same per codeword, so the stages of thousands of
+ * codewords of different (n, k, field, shard size) are run as one queue of
+ * tasks by a single persistent kernel.)
+ *
+ * A codeword: `shards` is a DEVICE pointer to n rows of shard_bytes (layout
+ * and rules as for rs_encode/rs_decode, n <= 8192); `erasure_mask` is a HOST
+ * array of n bytes (nonzero = erased) for decoding, ignored for encoding. */
+typedef struct lch_codeword {
+    uint32_t n;
+    uint32_t k;
+    int field;
+    uint32_t reserved; /* must be 0 */
+    size_t shard_bytes;
+    void *shards;
+    const uint8_t *erasure_mask;
+} lch_codeword;
+
+#define LCH_BATCH_ENCODE 0
+#define LCH_BATCH_DECODE 1
+
+typedef struct lch_batch lch_batch;
+
+/* Plan a batch: validates every codeword (the first invalid one fails the
+ * call with its index in lch_last_error), copies the erasure masks, builds the
+ * task queue and allocates the batch's device memory (queue, counters and the
+ * per-codeword scratch, about 2 n shard_bytes per decoded codeword and
+ * k shard_bytes per encoded one).  The plan is tied to these buffers: running
+ * it again recomputes the same codewords from the buffers' current contents.
+ * Synchronises the device once.  Decoding a codeword without erasures is a
+ * no-op; more than n - k erasures fail with LCH_ETOOMANY. */
+LCH_API int lch_batch_create(lch_ctx *ctx, int op, const lch_codeword *cws, uint32_t count, lch_batch **out);
+
+/* Enqueue one run of the batch on `stream`: a counter reset and one launch
+ * of the persistent kernel.  Allocates nothing and does not synchronise, so
+ * it can be recorded into a CUDA graph and replayed. */
+LCH_API int lch_batch_run(lch_ctx *ctx, lch_batch *batch, void *stream);
+
+/* Wait for the device and report whether the last run completed: LCH_OK, or
+ * LCH_ECUDA if a task gave up waiting for its predecessors (the kernel then
+ * drains without finishing; the outputs are undefined). */
+LCH_API int lch_batch_status(lch_ctx *ctx, lch_batch *batch);
+
+/* Number of tasks in the plan (diagnostics). */
+LCH_API uint32_t lch_batch_tasks(const lch_batch *batch);
+
+LCH_API void lch_batch_destroy(lch_batch *batch);
+
 /* Static text for a status code. */
 LCH_API const char *lch_strerror(int status);
 

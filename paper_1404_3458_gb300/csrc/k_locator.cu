@@ -23,49 +23,6 @@ namespace lch {
 
 namespace {
 
-__device__ __forceinline__ uint32_t madd(uint32_t a, uint32_t b, uint32_t M)
-{
-    uint32_t s = a + b;
-    return s >= M ? s - M : s;
-}
-__device__ __forceinline__ uint32_t msub(uint32_t a, uint32_t b, uint32_t M) { return a >= b ? a - b : a + M - b; }
-template <int R> __device__ __forceinline__ uint32_t mmul(uint32_t a, uint32_t b)
-{
-    constexpr uint32_t M = (1u << R) - 1;
-    uint64_t p = (uint64_t)a * b; // a, b < M, so p < 2^(2R)
-    p = (p & M) + (p >> R);
-    p = (p & M) + (p >> R);
-    return p >= M ? (uint32_t)(p - M) : (uint32_t)p;
-}
-
-__device__ __forceinline__ uint32_t mask_bit(const MaskBits &b, uint32_t j) { return (b.w[j >> 5] >> (j & 31u)) & 1u; }
-
-// In-place FWHT mod M of v[0 .. 2^lg) in shared memory.
-template <int R> __device__ void fwht_smem(uint32_t *v, uint32_t lg)
-{
-    constexpr uint32_t M = (1u << R) - 1;
-    const uint32_t half = (1u << lg) >> 1;
-    for (uint32_t lev = 0; lev < lg; lev++) {
-        for (uint32_t p = threadIdx.x; p < half; p += blockDim.x) {
-            uint32_t i = ((p >> lev) << (lev + 1)) | (p & ((1u << lev) - 1u));
-            uint32_t j = i + (1u << lev);
-            uint32_t x = v[i], y = v[j];
-            v[i] = madd(x, y, M);
-            v[j] = msub(x, y, M);
-        }
-        __syncthreads();
-    }
-}
-
-template <int R>
-__device__ __forceinline__ void emit(uint32_t j, uint32_t c, uint32_t erased, const uint16_t *__restrict__ expt,
-                                     uint16_t *pre, uint16_t *post)
-{
-    constexpr uint32_t M = (1u << R) - 1;
-    pre[j] = erased ? 0 : expt[c];
-    post[j] = erased ? expt[c == 0 ? 0 : M - c] : 0;
-}
-
 // MODE 0: FWHT(L) -> fl_out.  MODE 1: full locator -> pre/post.
 template <int R, int MODE>
 __global__ void __launch_bounds__(1024) k_loc_small(uint32_t lgn, MaskBits bits, const uint16_t *__restrict__ logt,

@@ -208,25 +208,25 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // One CTA per SM: the factor records of a row group stay in shared memory
 // while the CTA walks its column tiles; tile t+1 is copied in (cp.async)
 // while tile t is transformed.
 template <int R, int INV>
-__global__ void __launch_bounds__(kPassThreads, 1) k_pass(PassArgs a, uint32_t lg_cw)
+__device__ __forceinline__ void pass_body(const PassArgs &a, uint32_t lg_cw, uint32_t g, uint32_t y0, uint32_t ystep,
+                                          uint8_t *sm)
 {
-    extern __shared__ __align__(128) uint8_t sm[];
     const uint32_t nlev = a.nlev, nrows = 1u << nlev, nrec = nrows - 1;
     uint8_t *tab = sm;
     const uint32_t stab = (uint32_t)__cvta_generic_to_shared(sm);
     const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
     uint8_t *const buf0 = sm + tab_bytes<R>(nrec);
     const uint32_t tile_bytes = nrows << lg_cw;
-    const uint32_t g = blockIdx.x;
     const uint32_t lo = g & ((1u << a.L0) - 1u);
     const uint32_t hibase = (g >> a.L0) << (a.L0 + nlev);
-    const size_t col_step = (size_t)gridDim.y << lg_cw;
-    const size_t col0 = (size_t)blockIdx.y << lg_cw;
+    const size_t col_step = (size_t)ystep << lg_cw;
+    const size_t col0 = (size_t)y0 << lg_cw;
     const uint32_t ntiles = col0 < a.S ? (uint32_t)((a.S - col0 + col_step - 1) / col_step) : 0;
 
     // Stage the factor records of this row group (first copy group).
@@ -303,6 +303,15 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(PassArgs a, uint32_t l
         if (t + 2 < ntiles) issue(t + 2, data);
         cp_async_commit();
     }
+    cp_async_wait_all();
+    __syncthreads();
+}
+
+template <int R, int INV>
+__global__ void __launch_bounds__(kPassThreads, 1) k_pass(PassArgs a, uint32_t lg_cw)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
+    pass_body<R, INV>(a, lg_cw, blockIdx.x, blockIdx.y, gridDim.y, sm);
 }
 
 __global__ void __launch_bounds__(kThreads) k_superset(SupersetArgs a, uint32_t lg_cw)
@@ -474,9 +483,9 @@ __device__ __forceinline__ void deriv_round_q(uint32_t q, const DerivArgs &a, ui
 }
 
 template <int R, int MODE>
-__global__ void __launch_bounds__(kPassThreads, 1) k_deriv(DerivArgs a, uint32_t lg_cw)
+__device__ __forceinline__ void deriv_body(const DerivArgs &a, uint32_t lg_cw, uint32_t g, uint32_t y0, uint32_t ystep,
+                                           uint8_t *sm)
 {
-    extern __shared__ __align__(128) uint8_t sm[];
     constexpr bool kX = MODE == 1, kInv = MODE != 0;
     const uint32_t nlev = a.nlev, nrows = 1u << nlev;
     const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
@@ -486,11 +495,10 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_deriv(DerivArgs a, uint32_t
     uint8_t *stage0 = sm + (kInv ? 2 : 1) * rec_bytes;
     const uint32_t tile_bytes = nrows << lg_cw;
     const uint32_t stage_bytes = 2 * tile_bytes; // u tile + accumulator tile
-    const uint32_t g = blockIdx.x;
     const uint32_t lo = g & ((1u << a.L0) - 1u);
     const uint32_t hibase = (g >> a.L0) << (a.L0 + nlev);
-    const size_t col_step = (size_t)gridDim.y << lg_cw;
-    const size_t col0 = (size_t)blockIdx.y << lg_cw;
+    const size_t col_step = (size_t)ystep << lg_cw;
+    const size_t col0 = (size_t)y0 << lg_cw;
     const uint32_t ntiles = col0 < a.S ? (uint32_t)((a.S - col0 + col_step - 1) / col_step) : 0;
 
     // Records of the tile rows, laid out by sub-table (see nib_ref).
@@ -563,6 +571,15 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_deriv(DerivArgs a, uint32_t
         if (t + 2 < ntiles) issue(t + 2, stage);
         cp_async_commit();
     }
+    cp_async_wait_all();
+    __syncthreads();
+}
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(kPassThreads, 1) k_deriv(DerivArgs a, uint32_t lg_cw)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
+    deriv_body<R, MODE>(a, lg_cw, blockIdx.x, blockIdx.y, gridDim.y, sm);
 }
 
 template <int R>
@@ -642,6 +659,147 @@ cudaError_t pass_impl(const PassArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- batches
+
+// Rows [r0, r1) of a per-row scaling (see k_rowscale); the row's split table
+// is built in shared memory.  Global loads bypass L1 (data written by other
+// SMs earlier in the same launch).
+template <int R>
+__device__ __forceinline__ void rows_body(const BatchOp &op, uint32_t r0, uint32_t r1, uint8_t *sm)
+{
+    const size_t S = op.S;
+    for (uint32_t row = r0; row < r1; row++) {
+        const uint32_t c = __ldcg(op.coef + row);
+        uint4 *d4 = reinterpret_cast<uint4 *>(op.dst + (size_t)row * S);
+        if (c == 0) {
+            if (!op.mode)
+                for (size_t v = threadIdx.x; v < S / 16; v += blockDim.x) d4[v] = make_uint4(0, 0, 0, 0);
+            continue;
+        }
+        for (uint32_t idx = threadIdx.x; idx < FT<R>::rec_entries; idx += blockDim.x)
+            rec_store<R>(sm, idx, rec_entry<R>(c, idx));
+        __syncthreads();
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(op.src + (size_t)row * S);
+        for (size_t v = threadIdx.x; v < S / 16; v += blockDim.x) {
+            uint4 x = __ldcg(s4 + v);
+            x.x = mul_word<R>(x.x, sm);
+            x.y = mul_word<R>(x.y, sm);
+            x.z = mul_word<R>(x.z, sm);
+            x.w = mul_word<R>(x.w, sm);
+            d4[v] = x;
+        }
+        __syncthreads();
+    }
+}
+
+// Locator of one codeword (n <= 2^kBatchMaxLgn) in shared memory (Appendix).
+template <int R>
+__device__ __forceinline__ void locator_body(const BatchOp &op, uint8_t *sm)
+{
+    constexpr uint32_t M = (1u << R) - 1;
+    uint32_t *v = reinterpret_cast<uint32_t *>(sm);
+    const uint32_t lgn = op.L0, n = 1u << lgn;
+    const uint32_t ninv = (uint32_t)((1ull << (R - lgn)) % M);
+    const uint32_t *fl = reinterpret_cast<const uint32_t *>(op.tab0);
+    const uint16_t *expt = reinterpret_cast<const uint16_t *>(op.tab1);
+    for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) v[j] = (op.mask[j >> 5] >> (j & 31u)) & 1u;
+    __syncthreads();
+    fwht_smem<R>(v, lgn);
+    for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) v[j] = mmul<R>(v[j], fl[j]);
+    __syncthreads();
+    fwht_smem<R>(v, lgn);
+    for (uint32_t j = threadIdx.x; j < n; j += blockDim.x)
+        emit<R>(j, mmul<R>(v[j], ninv), (op.mask[j >> 5] >> (j & 31u)) & 1u, expt, op.pre, op.post);
+    __syncthreads();
+}
+
+template <int R>
+__device__ __forceinline__ void run_task(const BatchOp &op, const BatchTask &t, uint8_t *sm)
+{
+    switch (op.type) {
+    case kOpLocator: locator_body<R>(op, sm); break;
+    case kOpRows: rows_body<R>(op, t.g0, t.g1, sm); break;
+    case kOpPass: {
+        PassArgs a{op.src, op.dst, op.S, op.h, op.L0, op.nlev, op.l, (int)op.mode, op.tab0};
+        for (uint32_t g = t.g0; g < t.g1; g++)
+            if (op.mode)
+                pass_body<R, 1>(a, op.lg_cw, g, 0, 1, sm);
+            else
+                pass_body<R, 0>(a, op.lg_cw, g, 0, 1, sm);
+        break;
+    }
+    default: {
+        DerivArgs a{op.src, op.xin, op.dst, op.S, op.h, op.L0, op.nlev, op.tab0, op.tab1};
+        for (uint32_t g = t.g0; g < t.g1; g++) {
+            if (op.mode == 0)
+                deriv_body<R, 0>(a, op.lg_cw, g, 0, 1, sm);
+            else if (op.mode == 1)
+                deriv_body<R, 1>(a, op.lg_cw, g, 0, 1, sm);
+            else
+                deriv_body<R, 2>(a, op.lg_cw, g, 0, 1, sm);
+        }
+        break;
+    }
+    }
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+constexpr uint32_t kMaxWaitSpins = 1u << 24; // ~1-2 s with the back-off below
+
+// Shared memory of the largest task body: the second derivative pass of
+// GF(2^16) (2 x 256 nibble records + 2 stages of 2 tiles).
+__host__ __device__ constexpr size_t batch_body_smem() { return 2 * 256 * NibRec<16>::bytes + 4 * (size_t)kTileBytes; }
+
+// The persistent batch kernel: one CTA per SM pulls tasks in queue order.
+__global__ void __launch_bounds__(kPassThreads, 1)
+    k_batch(const BatchOp *__restrict__ ops, const BatchTask *__restrict__ tasks, uint32_t ntasks,
+            BatchCounters *ctr, uint32_t *done)
+{
+    // No static shared variables: the bodies address their tables with
+    // (index | base), which needs the dynamic region to start 128-byte aligned.
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint32_t &s_task = *reinterpret_cast<uint32_t *>(sm + batch_body_smem());
+    uint32_t &s_abort = *reinterpret_cast<uint32_t *>(sm + batch_body_smem() + 4);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_abort = ld_acquire(&ctr->err);
+            s_task = s_abort ? ntasks : atomicAdd(&ctr->next, 1u);
+        }
+        __syncthreads();
+        const uint32_t ti = s_task;
+        if (ti >= ntasks) break;
+        const BatchTask t = tasks[ti];
+        if (threadIdx.x == 0 && t.need) {
+            uint32_t spins = 0, ns = 32;
+            while (ld_acquire(done + t.cw) < t.need) {
+                __nanosleep(ns);
+                if (ns < 1024) ns <<= 1;
+                if (++spins > kMaxWaitSpins) { // give up: flag it and let every CTA drain
+                    atomicOr(&ctr->err, 1u);
+                    s_abort = 1;
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        const BatchOp op = ops[t.op];
+        if (op.field == 8)
+            run_task<8>(op, t, sm);
+        else
+            run_task<16>(op, t, sm);
+        __threadfence(); // publish this task's global writes ...
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(done + t.cw, 1u); // ... before counting it done
+    }
+}
+
 } // namespace
 
 cudaError_t configure_transform_kernels()
@@ -658,7 +816,21 @@ cudaError_t configure_transform_kernels()
     if ((e = cudaFuncSetAttribute(k_deriv<16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes())))
+        return e;
     return cudaFuncSetAttribute(k_superset, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
+uint32_t plan_lg_cw(uint32_t nrows, size_t S) { return pick_lg_cw(nrows, S); }
+
+size_t batch_smem_bytes() { return batch_body_smem() + 16; } // + the queue control words
+
+cudaError_t launch_batch(const BatchOp *ops, const BatchTask *tasks, uint32_t ntasks, BatchCounters *counters,
+                         uint32_t *done, uint32_t ctas, cudaStream_t s, uint64_t *launches)
+{
+    k_batch<<<ctas, kPassThreads, batch_smem_bytes(), s>>>(ops, tasks, ntasks, counters, done);
+    *launches += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pass(int r, const PassArgs &a, cudaStream_t s, uint64_t *launches)

@@ -3,6 +3,7 @@
 // transform, derivative, encoder (Algorithm 1) and decoder (Algorithm 2).
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -335,6 +336,203 @@ int encode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
     return LCH_OK;
 }
 
+// ---------------------------------------------------------------- batch planner
+
+constexpr size_t kTaskBytes = 512 * 1024; // target data per task
+
+struct PlanTask {
+    uint32_t stage, op, cw, g0, g1;
+    uint64_t cost;
+};
+
+// Built twice: once with null bases to size the batch's scratch and mask
+// arrays, then with the allocated device bases.
+struct Planner {
+    lch_ctx *ctx;
+    uint8_t *scratch_base = nullptr;
+    uint32_t *mask_base = nullptr;
+    std::vector<BatchOp> ops;
+    std::vector<PlanTask> tasks;
+    std::vector<uint32_t> masks; // packed erasure bitmaps
+    size_t scratch = 0;          // bytes reserved so far
+
+    uint8_t *reserve(size_t bytes)
+    {
+        uint8_t *p = scratch_base + scratch;
+        scratch += align_up(bytes);
+        return p;
+    }
+    uint32_t add_op(const BatchOp &op)
+    {
+        ops.push_back(op);
+        return (uint32_t)ops.size() - 1;
+    }
+    // Split an op over `units` rows or row groups of `unit_bytes` each.
+    void add_tasks(uint32_t stage, uint32_t op, uint32_t cw, uint32_t units, size_t unit_bytes)
+    {
+        const uint32_t per = (uint32_t)std::max<size_t>(1, kTaskBytes / std::max<size_t>(1, unit_bytes));
+        for (uint32_t g = 0; g < units; g += per) {
+            const uint32_t g1 = std::min(units, g + per);
+            tasks.push_back({stage, op, cw, g, g1, (uint64_t)(g1 - g) * unit_bytes});
+        }
+    }
+    // Transform passes of an h-point transform as in transform(); returns the
+    // next free stage.
+    uint32_t add_transform(uint32_t stage, uint32_t cw, int field, uint32_t h, uint32_t l, int inverse,
+                           const uint8_t *src, uint8_t *dst, size_t S)
+    {
+        uint32_t a, b;
+        split_levels(lg2(h), &a, &b);
+        uint32_t L0[2] = {inverse ? 0u : a, inverse ? a : 0u}, nl[2] = {inverse ? a : b, inverse ? b : a};
+        if (b == 0) {
+            L0[0] = 0;
+            nl[0] = a;
+        }
+        for (int p = 0; p < (b ? 2 : 1); p++) {
+            BatchOp op{};
+            op.type = kOpPass;
+            op.field = field;
+            op.mode = inverse;
+            op.lg_cw = plan_lg_cw(1u << nl[p], S);
+            op.src = p == 0 ? src : dst;
+            op.dst = dst;
+            op.S = S;
+            op.h = h;
+            op.L0 = L0[p];
+            op.nlev = nl[p];
+            op.l = l;
+            op.tab0 = ctx->tab[field == LCH_GF16].rec;
+            add_tasks(stage + p, add_op(op), cw, h >> nl[p], ((size_t)1 << nl[p]) * S);
+        }
+        return stage + (b ? 2 : 1);
+    }
+};
+
+void plan_decode(Planner &P, uint32_t cw, uint32_t n, int field, uint8_t *shards, size_t S, const uint8_t *mask)
+{
+    const uint32_t lgn = lg2(n);
+    const FieldTables &t = P.ctx->tab[field == LCH_GF16];
+    uint8_t *phi = P.reserve((size_t)n * S), *phi2 = P.reserve((size_t)n * S);
+    uint16_t *pre = reinterpret_cast<uint16_t *>(P.reserve(sizeof(uint16_t) * n));
+    uint16_t *post = reinterpret_cast<uint16_t *>(P.reserve(sizeof(uint16_t) * n));
+    const size_t moff = P.masks.size();
+    P.masks.resize(moff + ((n + 31) / 32), 0u);
+    for (uint32_t j = 0; j < n; j++)
+        if (mask[j]) P.masks[moff + (j >> 5)] |= 1u << (j & 31);
+    uint32_t stage = 0;
+    BatchOp loc{};
+    loc.type = kOpLocator;
+    loc.field = field;
+    loc.L0 = lgn;
+    loc.h = n;
+    loc.tab0 = reinterpret_cast<const uint8_t *>(P.ctx->fl[field == LCH_GF16][lgn]);
+    loc.tab1 = reinterpret_cast<const uint8_t *>(t.expt);
+    loc.mask = P.mask_base + moff;
+    loc.pre = pre;
+    loc.post = post;
+    P.tasks.push_back({stage++, P.add_op(loc), cw, 0, 1, (uint64_t)n * 64});
+    BatchOp rows{};
+    rows.type = kOpRows;
+    rows.field = field;
+    rows.S = S;
+    rows.src = shards;
+    rows.dst = phi;
+    rows.coef = pre;
+    rows.mode = 0;
+    P.add_tasks(stage++, P.add_op(rows), cw, n, S);
+    stage = P.add_transform(stage, cw, field, n, 0, 1, phi, phi, S);
+    uint32_t a, b;
+    split_levels(lgn, &a, &b);
+    BatchOp d{};
+    d.type = kOpDeriv;
+    d.field = field;
+    d.S = S;
+    d.h = n;
+    d.src = phi;
+    d.tab0 = t.bnib;
+    d.tab1 = t.binvnib;
+    if (b == 0) {
+        d.mode = 2;
+        d.dst = phi2;
+        d.L0 = 0;
+        d.nlev = a;
+        d.lg_cw = plan_lg_cw(1u << a, S);
+        P.add_tasks(stage++, P.add_op(d), cw, n >> a, ((size_t)1 << a) * S);
+    } else {
+        d.mode = 0;
+        d.dst = phi2;
+        d.L0 = 0;
+        d.nlev = a;
+        d.lg_cw = plan_lg_cw(1u << a, S);
+        P.add_tasks(stage++, P.add_op(d), cw, n >> a, ((size_t)1 << a) * S);
+        d.mode = 1;
+        d.xin = phi2;
+        d.L0 = a;
+        d.nlev = b;
+        d.lg_cw = plan_lg_cw(1u << b, S);
+        P.add_tasks(stage++, P.add_op(d), cw, n >> b, ((size_t)1 << b) * S);
+    }
+    stage = P.add_transform(stage, cw, field, n, 0, 0, phi2, phi2, S);
+    rows.src = phi2;
+    rows.dst = shards;
+    rows.coef = post;
+    rows.mode = 1;
+    P.add_tasks(stage++, P.add_op(rows), cw, n, S);
+}
+
+// All codewords of a batch into P (see Planner).
+void plan_batch(Planner &P, int op, const lch_codeword *cws, uint32_t count)
+{
+    std::vector<uint8_t> mask_buf;
+    for (uint32_t c = 0; c < count; c++) {
+        const lch_codeword &w = cws[c];
+        uint8_t *sh = static_cast<uint8_t *>(w.shards);
+        const size_t S = w.shard_bytes;
+        if (op == LCH_BATCH_DECODE) {
+            bool any = false;
+            for (uint32_t j = 0; j < w.n && !any; j++) any = w.erasure_mask[j] != 0;
+            if (any) plan_decode(P, c, w.n, w.field, sh, S, w.erasure_mask);
+        } else if (w.k == w.n) {
+            continue;
+        } else if (!is_pow2(w.k) || w.k == 1) { // shortened code: parity rows as erasures
+            mask_buf.assign(w.n, 0);
+            std::fill(mask_buf.begin() + w.k, mask_buf.end(), 1);
+            plan_decode(P, c, w.n, w.field, sh, S, mask_buf.data());
+        } else { // Algorithm 1
+            uint8_t *mbar = P.reserve((size_t)w.k * S);
+            const uint32_t st = P.add_transform(0, c, w.field, w.k, 0, 1, sh, mbar, S);
+            for (uint32_t i = 1; i < w.n / w.k; i++)
+                P.add_transform(st, c, w.field, w.k, i * w.k, 0, mbar, sh + (size_t)i * w.k * S, S);
+        }
+    }
+}
+
+} // namespace
+
+struct lch_batch {
+    uint32_t ncw = 0, ntasks = 0, ctas = 0;
+    BatchOp *ops = nullptr;
+    BatchTask *tasks = nullptr;
+    uint8_t *counters = nullptr; // BatchCounters + done[ncw]
+    size_t counter_bytes = 0;
+    uint32_t *masks = nullptr;
+    uint8_t *scratch = nullptr;
+    int device = 0;
+};
+
+namespace {
+
+void batch_free(lch_batch *b)
+{
+    if (!b) return;
+    cudaFree(b->ops);
+    cudaFree(b->tasks);
+    cudaFree(b->counters);
+    cudaFree(b->masks);
+    cudaFree(b->scratch);
+    delete b;
+}
+
 } // namespace
 
 void lch::set_last_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
@@ -453,6 +651,145 @@ LCH_API int rs_decode(lch_ctx *ctx, uint32_t n, uint32_t k, int field, void *sha
     DeviceScope ds(ctx->device);
     if (!ds.ok) return fail(LCH_ECUDA, "cannot select device %d", ctx->device);
     return decode_impl(ctx, n, k, field, (uint8_t *)shards, shard_bytes, erasure_mask, (cudaStream_t)stream);
+}
+
+
+LCH_API int lch_batch_create(lch_ctx *ctx, int op, const lch_codeword *cws, uint32_t count, lch_batch **out)
+{
+    if (!out) return fail(LCH_EINVAL, "output pointer is NULL");
+    *out = nullptr;
+    if (!ctx) return fail(LCH_EINVAL, "ctx is NULL");
+    if (op != LCH_BATCH_ENCODE && op != LCH_BATCH_DECODE) return fail(LCH_EINVAL, "op must be LCH_BATCH_ENCODE or LCH_BATCH_DECODE");
+    if (count && !cws) return fail(LCH_EINVAL, "codeword array is NULL");
+    for (uint32_t c = 0; c < count; c++) {
+        const lch_codeword &w = cws[c];
+        int rc;
+        if ((rc = check_field(w.field)) || (rc = check_len("n", w.n, w.field)) ||
+            (rc = check_buffer(w.shards, w.n, w.shard_bytes))) {
+            char why[sizeof(g_err)];
+            snprintf(why, sizeof(why), "%s", g_err);
+            return fail(rc, "codeword %u: %s", c, why);
+        }
+        if (w.n > (1u << kBatchMaxLgn)) return fail(LCH_EINVAL, "codeword %u: batched codewords need n <= %u", c, 1u << kBatchMaxLgn);
+        if (w.k == 0 || w.k > w.n) return fail(LCH_EINVAL, "codeword %u: k must satisfy 1 <= k <= n", c);
+        if (w.reserved) return fail(LCH_EINVAL, "codeword %u: reserved field must be 0", c);
+        if (op == LCH_BATCH_DECODE) {
+            if (!w.erasure_mask) return fail(LCH_EINVAL, "codeword %u: erasure_mask is NULL", c);
+            uint32_t ne = 0;
+            for (uint32_t j = 0; j < w.n; j++) ne += w.erasure_mask[j] != 0;
+            if (ne > w.n - w.k) return fail(LCH_ETOOMANY, "codeword %u: %u erasures exceed n - k = %u", c, ne, w.n - w.k);
+        }
+    }
+    DeviceScope ds(ctx->device);
+    if (!ds.ok) return fail(LCH_ECUDA, "cannot select device %d", ctx->device);
+    cudaStream_t s = 0;
+    int rc;
+    // tables and FWHT(log) for every (field, lg n) in the batch
+    if ((rc = ensure_scratch(ctx, sizeof(uint32_t) << kBatchMaxLgn))) return rc;
+    for (uint32_t c = 0; c < count; c++) {
+        if ((rc = ensure_tables(ctx, cws[c].field, s))) return rc;
+        if ((rc = ensure_fl(ctx, cws[c].field, lg2(cws[c].n), reinterpret_cast<uint32_t *>(ctx->scratch), s))) return rc;
+    }
+    Planner sizing{ctx};
+    plan_batch(sizing, op, cws, count);
+    lch_batch *b = new (std::nothrow) lch_batch;
+    if (!b) return fail(LCH_ENOMEM, "host allocation failed");
+    b->ncw = count;
+    b->device = ctx->device;
+    b->counter_bytes = sizeof(BatchCounters) + sizeof(uint32_t) * std::max<uint32_t>(1, count);
+    auto dev_alloc = [&](void **p, size_t bytes) -> int {
+        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LCH_ENOMEM, "batch allocation of %zu bytes failed", bytes);
+        }
+        return LCH_OK;
+    };
+    if ((rc = dev_alloc((void **)&b->scratch, sizing.scratch)) ||
+        (rc = dev_alloc((void **)&b->masks, sizing.masks.size() * 4)) ||
+        (rc = dev_alloc((void **)&b->ops, sizing.ops.size() * sizeof(BatchOp))) ||
+        (rc = dev_alloc((void **)&b->tasks, sizing.tasks.size() * sizeof(BatchTask))) ||
+        (rc = dev_alloc((void **)&b->counters, b->counter_bytes))) {
+        batch_free(b);
+        return rc;
+    }
+    Planner P{ctx, b->scratch, b->masks};
+    plan_batch(P, op, cws, count);
+    // stage-major queue, largest tasks first within a stage
+    std::stable_sort(P.tasks.begin(), P.tasks.end(), [](const PlanTask &x, const PlanTask &y) {
+        return x.stage != y.stage ? x.stage < y.stage : x.cost > y.cost;
+    });
+    // need = number of the codeword's tasks in earlier stages
+    std::vector<std::vector<uint32_t>> before(count);
+    for (const PlanTask &t : P.tasks) {
+        auto &v = before[t.cw];
+        if (v.size() <= t.stage) v.resize(t.stage + 1, 0);
+        v[t.stage]++;
+    }
+    for (auto &v : before) {
+        uint32_t acc = 0;
+        for (auto &x : v) {
+            const uint32_t here = x;
+            x = acc;
+            acc += here;
+        }
+    }
+    std::vector<BatchTask> tasks(P.tasks.size());
+    for (size_t i = 0; i < P.tasks.size(); i++) {
+        const PlanTask &t = P.tasks[i];
+        tasks[i] = {t.op, t.cw, before[t.cw][t.stage], t.g0, t.g1};
+    }
+    b->ntasks = (uint32_t)tasks.size();
+    auto upload = [&](void *dst, const void *src, size_t bytes) -> int {
+        if (bytes && cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            batch_free(b);
+            return cuda_fail(cudaGetLastError(), "batch upload");
+        }
+        return LCH_OK;
+    };
+    if ((rc = upload(b->masks, P.masks.data(), P.masks.size() * 4)) ||
+        (rc = upload(b->ops, P.ops.data(), P.ops.size() * sizeof(BatchOp))) ||
+        (rc = upload(b->tasks, tasks.data(), tasks.size() * sizeof(BatchTask))))
+        return rc;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || sms < 1) sms = 1;
+    b->ctas = (uint32_t)sms; // one CTA per SM (the kernel uses ~192 KB of shared memory)
+    *out = b;
+    return LCH_OK;
+}
+
+LCH_API int lch_batch_run(lch_ctx *ctx, lch_batch *b, void *stream)
+{
+    if (!ctx || !b) return fail(LCH_EINVAL, "ctx or batch is NULL");
+    DeviceScope ds(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (b->ntasks == 0) return LCH_OK;
+    CU(cudaMemsetAsync(b->counters, 0, b->counter_bytes, s), "counter reset");
+    BatchCounters *ctr = reinterpret_cast<BatchCounters *>(b->counters);
+    uint32_t *done = reinterpret_cast<uint32_t *>(b->counters + sizeof(BatchCounters));
+    CU(launch_batch(b->ops, b->tasks, b->ntasks, ctr, done, b->ctas, s, &ctx->launches), "batch launch");
+    return LCH_OK;
+}
+
+LCH_API int lch_batch_status(lch_ctx *ctx, lch_batch *b)
+{
+    if (!ctx || !b) return fail(LCH_EINVAL, "ctx or batch is NULL");
+    DeviceScope ds(ctx->device);
+    CU(cudaDeviceSynchronize(), "batch");
+    if (b->ntasks == 0) return LCH_OK;
+    BatchCounters h{};
+    CU(cudaMemcpy(&h, b->counters, sizeof(h), cudaMemcpyDeviceToHost), "batch status");
+    if (h.err) return fail(LCH_ECUDA, "a batch task gave up waiting for its predecessors");
+    return LCH_OK;
+}
+
+LCH_API uint32_t lch_batch_tasks(const lch_batch *b) { return b ? b->ntasks : 0; }
+
+LCH_API void lch_batch_destroy(lch_batch *b)
+{
+    if (!b) return;
+    DeviceScope ds(b->device);
+    cudaDeviceSynchronize();
+    batch_free(b);
 }
 
 LCH_API const char *lch_strerror(int status)

@@ -199,10 +199,89 @@ constexpr uint32_t kMaxN = 65536;
 struct MaskBits {
     uint32_t w[kMaxN / 32];
 };
+// ---- locator arithmetic modulo 2^r - 1 (Appendix), shared by the locator kernels
+__device__ __forceinline__ uint32_t madd(uint32_t a, uint32_t b, uint32_t M)
+{
+    uint32_t s = a + b;
+    return s >= M ? s - M : s;
+}
+__device__ __forceinline__ uint32_t msub(uint32_t a, uint32_t b, uint32_t M) { return a >= b ? a - b : a + M - b; }
+template <int R> __device__ __forceinline__ uint32_t mmul(uint32_t a, uint32_t b)
+{
+    constexpr uint32_t M = (1u << R) - 1;
+    uint64_t p = (uint64_t)a * b; // a, b < M, so p < 2^(2R)
+    p = (p & M) + (p >> R);
+    p = (p & M) + (p >> R);
+    return p >= M ? (uint32_t)(p - M) : (uint32_t)p;
+}
+
+// In-place FWHT mod M of v[0 .. 2^lg) in shared memory.
+template <int R> __device__ void fwht_smem(uint32_t *v, uint32_t lg)
+{
+    constexpr uint32_t M = (1u << R) - 1;
+    const uint32_t half = (1u << lg) >> 1;
+    for (uint32_t lev = 0; lev < lg; lev++) {
+        for (uint32_t p = threadIdx.x; p < half; p += blockDim.x) {
+            uint32_t i = ((p >> lev) << (lev + 1)) | (p & ((1u << lev) - 1u));
+            uint32_t j = i + (1u << lev);
+            uint32_t x = v[i], y = v[j];
+            v[i] = madd(x, y, M);
+            v[j] = msub(x, y, M);
+        }
+        __syncthreads();
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void emit(uint32_t j, uint32_t c, uint32_t erased, const uint16_t *__restrict__ expt,
+                                     uint16_t *pre, uint16_t *post)
+{
+    constexpr uint32_t M = (1u << R) - 1;
+    pre[j] = erased ? 0 : expt[c];
+    post[j] = erased ? expt[c == 0 ? 0 : M - c] : 0;
+}
+
+__device__ __forceinline__ uint32_t mask_bit(const MaskBits &b, uint32_t j) { return (b.w[j >> 5] >> (j & 31u)) & 1u; }
+
 cudaError_t launch_fwht_log_table(int r, const FieldTables &t, uint32_t lgn, uint32_t *fl,
                                   uint32_t *work, cudaStream_t s, uint64_t *launches);
 cudaError_t launch_locator(int r, const FieldTables &t, uint32_t lgn, const MaskBits &bits,
                            const uint32_t *fl, uint32_t *work, uint16_t *pre, uint16_t *post,
                            cudaStream_t s, uint64_t *launches);
+
+// ---------------------------------------------------------------- batches
+// One persistent launch runs many codewords: tasks are pulled from a queue in
+// stage-major order; a task waits until its codeword's completion counter has
+// reached `need` (all tasks of the codeword's earlier stages), runs, and bumps
+// the counter.
+enum BatchOpType : uint32_t { kOpLocator = 0, kOpRows = 1, kOpPass = 2, kOpDeriv = 3 };
+struct BatchOp {
+    uint32_t type, field, mode, lg_cw;
+    const uint8_t *src;
+    const uint8_t *xin;
+    uint8_t *dst;
+    size_t S;
+    uint32_t h, L0, nlev, l;
+    const uint8_t *tab0;   // pass: factor records; deriv: B nibble records; locator: FWHT(L)
+    const uint8_t *tab1;   // deriv: B^-1 nibble records; locator: exp table
+    const uint16_t *coef;  // rows: per-row constants; locator: log table
+    const uint32_t *mask;  // locator: erasure bitmap (n bits)
+    uint16_t *pre, *post;  // locator outputs
+};
+struct BatchTask {
+    uint32_t op, cw, need, g0, g1; // rows/row groups [g0, g1) of op
+};
+struct BatchCounters {
+    uint32_t next; // queue head
+    uint32_t err;  // nonzero: a dependency wait gave up
+    uint32_t pad[2];
+    // followed by one completion counter per codeword
+};
+constexpr uint32_t kBatchMaxLgn = 13; // single-CTA locator per codeword
+size_t batch_smem_bytes();
+cudaError_t launch_batch(const BatchOp *ops, const BatchTask *tasks, uint32_t ntasks, BatchCounters *counters,
+                         uint32_t *done, uint32_t ctas, cudaStream_t s, uint64_t *launches);
+// Shared helpers of the planners.
+uint32_t plan_lg_cw(uint32_t nrows, size_t S);
 
 } // namespace lch

@@ -24,6 +24,16 @@ GF8, GF16 = 8, 16
 
 _lib = None
 
+BATCH_ENCODE, BATCH_DECODE = 0, 1
+
+
+class Codeword(ctypes.Structure):
+    """struct lch_codeword of include/lch.h."""
+
+    _fields_ = [("n", ctypes.c_uint32), ("k", ctypes.c_uint32), ("field", ctypes.c_int),
+                ("reserved", ctypes.c_uint32), ("shard_bytes", ctypes.c_size_t), ("shards", ctypes.c_void_p),
+                ("erasure_mask", ctypes.c_void_p)]
+
 
 class LchError(RuntimeError):
     def __init__(self, status: int, message: str):
@@ -58,6 +68,11 @@ def load() -> ctypes.CDLL:
         "lch_last_error": (ctypes.c_char_p, []),
         "lch_launch_count": (ctypes.c_uint64, [vp]),
         "lch_derivative_noalloc": (i, [i, u32, vp, sz, vp]),
+        "lch_batch_create": (i, [vp, i, vp, u32, ctypes.POINTER(vp)]),
+        "lch_batch_run": (i, [vp, vp, vp]),
+        "lch_batch_status": (i, [vp, vp]),
+        "lch_batch_tasks": (u32, [vp]),
+        "lch_batch_destroy": (None, [vp]),
         "lch_profile_enable": (i, [vp, i]),
         "lch_profile_read": (i, [vp, i, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
@@ -107,6 +122,50 @@ def derivative_noalloc(field: int, buf, stream=None):
     _check(load().lch_derivative_noalloc(field, buf.shape[0], p, S, _stream_handle(stream)))
 
 
+class Batch:
+    """A planned batch of codewords (lch_batch_create); run() enqueues one
+    persistent launch, status() waits and reports."""
+
+    def __init__(self, ctx, op, codewords):
+        """codewords: list of (n, k, field, shards_tensor, erasure_mask or None)."""
+        self._ctx = ctx
+        self._keep = []
+        arr = (Codeword * max(1, len(codewords)))()
+        for i, (n, k, field, shards, mask) in enumerate(codewords):
+            p, S = _buf(shards, n)
+            m = None
+            if mask is not None:
+                m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).reshape(-1))
+                if m.size != n:
+                    raise ValueError(f"codeword {i}: erasure mask must have n={n} entries")
+                self._keep.append(m)
+            arr[i] = Codeword(n, k, field, 0, S, p.value, None if m is None else m.ctypes.data)
+        h = ctypes.c_void_p()
+        _check(load().lch_batch_create(ctx._h, op, arr, len(codewords), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def tasks(self) -> int:
+        return int(load().lch_batch_tasks(self._h))
+
+    def run(self, stream=None):
+        _check(load().lch_batch_run(self._ctx._h, self._h, _stream_handle(stream)))
+
+    def status(self):
+        _check(load().lch_batch_status(self._ctx._h, self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lch_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Context:
     """A liblch context on one CUDA device (owns tables and scratch)."""
 
@@ -143,6 +202,9 @@ class Context:
         _check(load().lch_profile_read(self._h, kind, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by),
                                        ctypes.byref(mu)))
         return {"launches": int(n.value), "ms": float(ms.value), "bytes": int(by.value), "mults": int(mu.value)}
+
+    def batch(self, op: int, codewords) -> "Batch":
+        return Batch(self, op, codewords)
 
     # Sec. III: Psi_h^l and its inverse, in place on h rows.
     def fft(self, field: int, l: int, buf, stream=None):
