@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--workload", default="large_gf16", choices=sorted(WL.WORKLOADS))
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--batch-count", type=int, default=1024)
+    p.add_argument("--batch-reps", type=int, default=5)
     return p.parse_args()
 
 
@@ -292,11 +295,92 @@ def run_ours(args):
     }
     if e2e:
         out["e2e"] = e2e
+    if not args.no_batch:
+        out["batched"] = run_batch_compare(ctx, torch, args, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, n, k, S, ne)
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()
+
+
+def run_batch_compare(ctx, torch, args, rank):
+    """The batched mix (one persistent launch per encode and per decode,
+    replayed from a CUDA graph) against plain per-codeword launches of the same
+    codewords; inputs generated on the device from a seeded torch generator."""
+    from paper_1404_3458_gb300 import lch
+
+    specs = WL.batch_workload(args.batch_count, WL.SEED_BASE + 4 + rank)
+    offs, total = [], 0
+    for (r, n, k, S, e) in specs:
+        offs.append(total)
+        total += (n * S + 255) // 256 * 256
+    plain = torch.empty(total, dtype=torch.uint8, device="cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(WL.SEED_BASE + 40 + rank)
+    views = []
+    for (r, n, k, S, e), o in zip(specs, offs):
+        v = plain[o:o + n * S].view(n, S)
+        v[:k] = torch.randint(0, 256, (k, S), dtype=torch.uint8, device="cuda", generator=gen)
+        views.append(v)
+    batched = plain.clone()
+    bviews = [batched[o:o + n * S].view(n, S) for (r, n, k, S, e), o in zip(specs, offs)]
+    masks = [WL.erasure_mask(n, e, WL.SEED_BASE + 400 + i) for i, (r, n, k, S, e) in enumerate(specs)]
+    shard = sum(k * S for (r, n, k, S, e) in specs), sum(e * S for (r, n, k, S, e) in specs)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+
+    res = {}
+    for op, name in ((lch.BATCH_ENCODE, "encode"), (lch.BATCH_DECODE, "decode")):
+        if op == lch.BATCH_ENCODE:
+            def plain_fn():
+                for (r, n, k, S, e), v in zip(specs, views):
+                    ctx.rs_encode(n, k, r, v)
+        else:
+            def plain_fn():
+                for (r, n, k, S, e), v, m in zip(specs, views, masks):
+                    ctx.rs_decode(n, k, r, v, m)
+        plain_fn()
+        torch.cuda.synchronize()
+        tp = timed(plain_fn, args.batch_reps)
+        b = ctx.batch(op, [(n, k, r, v, (m if op == lch.BATCH_DECODE else None))
+                           for (r, n, k, S, e), v, m in zip(specs, bviews, masks)])
+        b.run()
+        b.status()
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                b.run(side)
+        stream.wait_stream(side)
+        tb = timed(graph.replay, args.batch_reps)
+        b.status()
+        same = bool(torch.equal(plain, batched))
+        byts = shard[0] if op == lch.BATCH_ENCODE else shard[1]
+        res[name] = {"plain_ms_p50": round(pct(tp, 50), 3), "plain_ms_p99": round(pct(tp, 99), 3),
+                     "batched_ms_p50": round(pct(tb, 50), 3), "batched_ms_p99": round(pct(tb, 99), 3),
+                     "plain_gbs": round(byts / (pct(tp, 50) / 1e3) / 1e9, 2),
+                     "batched_gbs": round(byts / (pct(tb, 50) / 1e3) / 1e9, 2),
+                     "tasks": b.tasks, "identical_to_plain": same}
+        b.close()
+    res["workload"] = (f"{args.batch_count} codewords: n=2^(6..13), k/n in {{1/2,1/4,3/4}}, GF(2^8) if n<=256 "
+                       "else GF(2^16), S in {512,2K,8K,16K}, erasures uniform in [0,n-k]; device-generated "
+                       "seeded data; batched = one persistent launch replayed from a CUDA graph")
+    res["shard_bytes"] = {"encode": shard[0], "decode": shard[1]}
+    del plain, batched
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_e2e(ctx, torch, host, mask, w, args):

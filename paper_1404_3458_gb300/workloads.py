@@ -67,3 +67,20 @@ def burst_mask(n: int, count: int, start: int) -> np.ndarray:
 
 def random_burst_start(n: int, count: int, seed: int) -> int:
     return int(rng(seed).integers(0, n - count + 1))
+
+
+def batch_workload(count: int, seed: int = SEED_BASE + 4):
+    """The batched mix: `count` codewords with n = 2^u, u uniform in 6..13,
+    k/n drawn from {1/2, 1/4, 3/4}, GF(2^8) when n <= 256 else GF(2^16),
+    shard bytes from {512, 2048, 8192, 16384} and an erasure count uniform in
+    [0, n-k].  Returns a list of (field, n, k, shard_bytes, erasures)."""
+    g = rng(seed)
+    out = []
+    for _ in range(count):
+        n = 1 << int(g.integers(6, 14))
+        k = n * [2, 1, 3][int(g.integers(0, 3))] // 4
+        field = 8 if n <= 256 else 16
+        S = [512, 2048, 8192, 16384][int(g.integers(0, 4))]
+        e = int(g.integers(0, n - k + 1))
+        out.append((field, n, k, S, e))
+    return out
