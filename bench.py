@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--batch-count", type=int, default=1024)
     p.add_argument("--batch-reps", type=int, default=5)
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=256)
     return p.parse_args()
 
 
@@ -297,6 +299,8 @@ def run_ours(args):
         out["e2e"] = e2e
     if not args.no_batch:
         out["batched"] = run_batch_compare(ctx, torch, args, rank)
+    if not args.no_serve:
+        out["serving"] = run_serving(ctx, torch, args, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, n, k, S, ne)
     if rank == 0:
@@ -381,6 +385,49 @@ def run_batch_compare(ctx, torch, args, rank):
     del plain, batched
     torch.cuda.empty_cache()
     return res
+
+
+def run_serving(ctx, torch, args, rank):
+    """Open-loop Poisson arrivals (70 % encode, 30 % decode, sizes from the
+    batched mix) served with continuous batching under a 40 GB device budget,
+    against one rs_encode/rs_decode call per request under the same budget."""
+    from paper_1404_3458_gb300 import lch
+    from paper_1404_3458_gb300 import serve as SV
+
+    N = args.serve_requests
+    specs = WL.batch_workload(N, WL.SEED_BASE + 5 + rank)
+    g = WL.rng(WL.SEED_BASE + 50 + rank)
+    ops = [lch.BATCH_ENCODE if g.random() < 0.7 else lch.BATCH_DECODE for _ in range(N)]
+    masks = [WL.erasure_mask(n, e, WL.SEED_BASE + 500 + i) for i, (r, n, k, S, e) in enumerate(specs)]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(WL.SEED_BASE + 51 + rank)
+    biggest = max(n * S for (r, n, k, S, e) in specs)
+    pool = torch.randint(0, 256, (biggest,), dtype=torch.uint8, device="cuda", generator=gen)
+    budget = 40 * 10**9
+    out = {"budget_bytes": budget, "requests_per_rate": N,
+           "workload": "Poisson arrivals, 70% encode / 30% decode, (n,k,field,S,erasures) as in the batched mix"}
+    for rate in (1e3, 1e4, 1e5):
+        arr = SV.poisson_arrivals(rate, N, WL.SEED_BASE + int(rate) + rank)
+        res = {}
+        for name in ("served", "plain"):
+            reqs = [SV.Request(i, ops[i], r, n, k, S, float(arr[i]),
+                               mask=(masks[i] if ops[i] == lch.BATCH_DECODE else None),
+                               payload=pool[:n * S].view(n, S))
+                    for i, (r, n, k, S, e) in enumerate(specs)]
+            torch.cuda.synchronize()
+            if name == "served":
+                srv = SV.Server(ctx, budget, max_inflight=2, max_batch=1024)
+                st = srv.run(reqs)
+                del srv
+            else:
+                st = SV.serve_plain(ctx, reqs, budget)
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            res[name] = {k2: (round(v, 3) if isinstance(v, float) else v) for k2, v in st.items()}
+        out[f"{int(rate)}_req_s"] = res
+    del pool
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_e2e(ctx, torch, host, mask, w, args):

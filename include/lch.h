@@ -164,14 +164,31 @@ typedef struct lch_batch lch_batch;
  * no-op; more than n - k erasures fail with LCH_ETOOMANY. */
 LCH_API int lch_batch_create(lch_ctx *ctx, int op, const lch_codeword *cws, uint32_t count, lch_batch **out);
 
+/* Device bytes (scratch, erasure bitmaps, task queue, counters) that
+ * lch_batch_create_in needs for these codewords.  Host-only; validates like
+ * lch_batch_create. */
+LCH_API int lch_batch_bytes(lch_ctx *ctx, int op, const lch_codeword *cws, uint32_t count, size_t *bytes);
+
+/* lch_batch_create without allocation: every device byte of the batch is
+ * placed in the caller's block [mem, mem + bytes) (256-byte aligned, at least
+ * lch_batch_bytes), and the plan is uploaded on `stream` without a device-wide
+ * synchronisation, so a server can plan a new batch from a memory arena while
+ * earlier batches still run.  The caller keeps the block, the shard buffers
+ * and the batch alive until the batch's runs have completed on the device.
+ * The first batch that uses a field or an n on the context still builds that
+ * field's tables (allocating and synchronising once). */
+LCH_API int lch_batch_create_in(lch_ctx *ctx, int op, const lch_codeword *cws, uint32_t count, void *mem,
+                                size_t bytes, void *stream, lch_batch **out);
+
 /* Enqueue one run of the batch on `stream`: a counter reset and one launch
  * of the persistent kernel.  Allocates nothing and does not synchronise, so
  * it can be recorded into a CUDA graph and replayed. */
 LCH_API int lch_batch_run(lch_ctx *ctx, lch_batch *batch, void *stream);
 
-/* Wait for the device and report whether the last run completed: LCH_OK, or
- * LCH_ECUDA if a task gave up waiting for its predecessors (the kernel then
- * drains without finishing; the outputs are undefined). */
+/* Wait for the stream of the batch's last run and report whether that run
+ * completed: LCH_OK, or LCH_ECUDA if a task gave up waiting for its
+ * predecessors (the kernel then drains without finishing; the outputs are
+ * undefined). */
 LCH_API int lch_batch_status(lch_ctx *ctx, lch_batch *batch);
 
 /* Number of tasks in the plan (diagnostics). */

@@ -517,7 +517,13 @@ struct lch_batch {
     size_t counter_bytes = 0;
     uint32_t *masks = nullptr;
     uint8_t *scratch = nullptr;
+    uint8_t *owned = nullptr; // device block allocated by lch_batch_create
+    cudaStream_t last = 0;    // stream of the last run
     int device = 0;
+    // host copies of the uploaded plan (kept until destroy)
+    std::vector<BatchOp> h_ops;
+    std::vector<BatchTask> h_tasks;
+    std::vector<uint32_t> h_masks;
 };
 
 namespace {
@@ -525,12 +531,145 @@ namespace {
 void batch_free(lch_batch *b)
 {
     if (!b) return;
-    cudaFree(b->ops);
-    cudaFree(b->tasks);
-    cudaFree(b->counters);
-    cudaFree(b->masks);
-    cudaFree(b->scratch);
+    cudaFree(b->owned);
     delete b;
+}
+
+// Device layout of a batch inside one block: scratch | masks | ops | tasks | counters.
+struct BatchLayout {
+    size_t scratch, masks, ops, tasks, counters, total;
+};
+BatchLayout batch_layout(const Planner &P, uint32_t count)
+{
+    BatchLayout L{};
+    L.scratch = 0;
+    L.masks = align_up(P.scratch);
+    L.ops = L.masks + align_up(std::max<size_t>(4, P.masks.size() * 4));
+    L.tasks = L.ops + align_up(std::max<size_t>(1, P.ops.size()) * sizeof(BatchOp));
+    L.counters = L.tasks + align_up(std::max<size_t>(1, P.tasks.size()) * sizeof(BatchTask));
+    L.total = L.counters + align_up(sizeof(BatchCounters) + sizeof(uint32_t) * std::max<uint32_t>(1, count));
+    return L;
+}
+
+int validate_batch(int op, const lch_codeword *cws, uint32_t count)
+{
+    if (op != LCH_BATCH_ENCODE && op != LCH_BATCH_DECODE) return fail(LCH_EINVAL, "op must be LCH_BATCH_ENCODE or LCH_BATCH_DECODE");
+    if (count && !cws) return fail(LCH_EINVAL, "codeword array is NULL");
+    for (uint32_t c = 0; c < count; c++) {
+        const lch_codeword &w = cws[c];
+        int rc;
+        if ((rc = check_field(w.field)) || (rc = check_len("n", w.n, w.field)) ||
+            (rc = check_buffer(w.shards, w.n, w.shard_bytes))) {
+            char why[sizeof(g_err)];
+            snprintf(why, sizeof(why), "%s", g_err);
+            return fail(rc, "codeword %u: %s", c, why);
+        }
+        if (w.n > (1u << kBatchMaxLgn)) return fail(LCH_EINVAL, "codeword %u: batched codewords need n <= %u", c, 1u << kBatchMaxLgn);
+        if (w.k == 0 || w.k > w.n) return fail(LCH_EINVAL, "codeword %u: k must satisfy 1 <= k <= n", c);
+        if (w.reserved) return fail(LCH_EINVAL, "codeword %u: reserved field must be 0", c);
+        if (op == LCH_BATCH_DECODE) {
+            if (!w.erasure_mask) return fail(LCH_EINVAL, "codeword %u: erasure_mask is NULL", c);
+            uint32_t ne = 0;
+            for (uint32_t j = 0; j < w.n; j++) ne += w.erasure_mask[j] != 0;
+            if (ne > w.n - w.k) return fail(LCH_ETOOMANY, "codeword %u: %u erasures exceed n - k = %u", c, ne, w.n - w.k);
+        }
+    }
+    return LCH_OK;
+}
+
+// Plan and upload a batch into [mem, mem + bytes) (mem == nullptr: allocate).
+int batch_create(lch_ctx *ctx, int op, const lch_codeword *cws, uint32_t count, uint8_t *mem, size_t bytes,
+                 cudaStream_t s, lch_batch **out)
+{
+    int rc;
+    if (!out) return fail(LCH_EINVAL, "output pointer is NULL");
+    *out = nullptr;
+    if (!ctx) return fail(LCH_EINVAL, "ctx is NULL");
+    if ((rc = validate_batch(op, cws, count))) return rc;
+    DeviceScope ds(ctx->device);
+    if (!ds.ok) return fail(LCH_ECUDA, "cannot select device %d", ctx->device);
+    // tables and FWHT(log) for every (field, lg n): built once per context
+    for (uint32_t c = 0; c < count; c++) {
+        const uint32_t lgn = lg2(cws[c].n);
+        if ((rc = ensure_tables(ctx, cws[c].field, s))) return rc;
+        if (!ctx->fl[cws[c].field == LCH_GF16][lgn]) {
+            if ((rc = ensure_scratch(ctx, sizeof(uint32_t) << kBatchMaxLgn))) return rc;
+            if ((rc = ensure_fl(ctx, cws[c].field, lgn, reinterpret_cast<uint32_t *>(ctx->scratch), s))) return rc;
+        }
+    }
+    Planner sizing{ctx};
+    plan_batch(sizing, op, cws, count);
+    const BatchLayout L = batch_layout(sizing, count);
+    lch_batch *b = new (std::nothrow) lch_batch;
+    if (!b) return fail(LCH_ENOMEM, "host allocation failed");
+    b->ncw = count;
+    b->device = ctx->device;
+    if (!mem) {
+        if (cudaMalloc(&b->owned, L.total) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return fail(LCH_ENOMEM, "batch allocation of %zu bytes failed", L.total);
+        }
+        mem = b->owned;
+    } else if (bytes < L.total || ((uintptr_t)mem & 255u)) {
+        delete b;
+        return fail(LCH_EINVAL, "batch memory must be 256-byte aligned and at least %zu bytes", L.total);
+    }
+    b->scratch = mem + L.scratch;
+    b->masks = reinterpret_cast<uint32_t *>(mem + L.masks);
+    b->ops = reinterpret_cast<BatchOp *>(mem + L.ops);
+    b->tasks = reinterpret_cast<BatchTask *>(mem + L.tasks);
+    b->counters = mem + L.counters;
+    b->counter_bytes = L.total - L.counters;
+    Planner P{ctx, b->scratch, b->masks};
+    plan_batch(P, op, cws, count);
+    // stage-major queue, largest tasks first within a stage
+    std::stable_sort(P.tasks.begin(), P.tasks.end(), [](const PlanTask &x, const PlanTask &y) {
+        return x.stage != y.stage ? x.stage < y.stage : x.cost > y.cost;
+    });
+    // need = number of the codeword's tasks in earlier stages
+    std::vector<std::vector<uint32_t>> before(count);
+    for (const PlanTask &t : P.tasks) {
+        auto &v = before[t.cw];
+        if (v.size() <= t.stage) v.resize(t.stage + 1, 0);
+        v[t.stage]++;
+    }
+    for (auto &v : before) {
+        uint32_t acc = 0;
+        for (auto &x : v) {
+            const uint32_t here = x;
+            x = acc;
+            acc += here;
+        }
+    }
+    b->h_tasks.resize(P.tasks.size());
+    for (size_t i = 0; i < P.tasks.size(); i++) {
+        const PlanTask &t = P.tasks[i];
+        b->h_tasks[i] = {t.op, t.cw, before[t.cw][t.stage], t.g0, t.g1};
+    }
+    b->h_ops = std::move(P.ops);
+    b->h_masks = std::move(P.masks);
+    b->ntasks = (uint32_t)b->h_tasks.size();
+    cudaError_t e = cudaSuccess;
+    if (!b->h_masks.empty()) e = cudaMemcpyAsync(b->masks, b->h_masks.data(), b->h_masks.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !b->h_ops.empty())
+        e = cudaMemcpyAsync(b->ops, b->h_ops.data(), b->h_ops.size() * sizeof(BatchOp), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !b->h_tasks.empty())
+        e = cudaMemcpyAsync(b->tasks, b->h_tasks.data(), b->h_tasks.size() * sizeof(BatchTask), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return cuda_fail(e, "batch upload");
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || sms < 1) sms = 1;
+    b->ctas = (uint32_t)sms; // one CTA per SM (the kernel uses ~192 KB of shared memory)
+    b->last = s;
+    if (b->owned && cudaStreamSynchronize(s) != cudaSuccess) {
+        batch_free(b);
+        return cuda_fail(cudaGetLastError(), "batch set-up");
+    }
+    *out = b;
+    return LCH_OK;
 }
 
 } // namespace
@@ -656,105 +795,25 @@ LCH_API int rs_decode(lch_ctx *ctx, uint32_t n, uint32_t k, int field, void *sha
 
 LCH_API int lch_batch_create(lch_ctx *ctx, int op, const lch_codeword *cws, uint32_t count, lch_batch **out)
 {
-    if (!out) return fail(LCH_EINVAL, "output pointer is NULL");
-    *out = nullptr;
-    if (!ctx) return fail(LCH_EINVAL, "ctx is NULL");
-    if (op != LCH_BATCH_ENCODE && op != LCH_BATCH_DECODE) return fail(LCH_EINVAL, "op must be LCH_BATCH_ENCODE or LCH_BATCH_DECODE");
-    if (count && !cws) return fail(LCH_EINVAL, "codeword array is NULL");
-    for (uint32_t c = 0; c < count; c++) {
-        const lch_codeword &w = cws[c];
-        int rc;
-        if ((rc = check_field(w.field)) || (rc = check_len("n", w.n, w.field)) ||
-            (rc = check_buffer(w.shards, w.n, w.shard_bytes))) {
-            char why[sizeof(g_err)];
-            snprintf(why, sizeof(why), "%s", g_err);
-            return fail(rc, "codeword %u: %s", c, why);
-        }
-        if (w.n > (1u << kBatchMaxLgn)) return fail(LCH_EINVAL, "codeword %u: batched codewords need n <= %u", c, 1u << kBatchMaxLgn);
-        if (w.k == 0 || w.k > w.n) return fail(LCH_EINVAL, "codeword %u: k must satisfy 1 <= k <= n", c);
-        if (w.reserved) return fail(LCH_EINVAL, "codeword %u: reserved field must be 0", c);
-        if (op == LCH_BATCH_DECODE) {
-            if (!w.erasure_mask) return fail(LCH_EINVAL, "codeword %u: erasure_mask is NULL", c);
-            uint32_t ne = 0;
-            for (uint32_t j = 0; j < w.n; j++) ne += w.erasure_mask[j] != 0;
-            if (ne > w.n - w.k) return fail(LCH_ETOOMANY, "codeword %u: %u erasures exceed n - k = %u", c, ne, w.n - w.k);
-        }
-    }
-    DeviceScope ds(ctx->device);
-    if (!ds.ok) return fail(LCH_ECUDA, "cannot select device %d", ctx->device);
-    cudaStream_t s = 0;
+    return batch_create(ctx, op, cws, count, nullptr, 0, 0, out);
+}
+
+LCH_API int lch_batch_bytes(lch_ctx *ctx, int op, const lch_codeword *cws, uint32_t count, size_t *bytes)
+{
+    if (!ctx || !bytes) return fail(LCH_EINVAL, "ctx or output pointer is NULL");
     int rc;
-    // tables and FWHT(log) for every (field, lg n) in the batch
-    if ((rc = ensure_scratch(ctx, sizeof(uint32_t) << kBatchMaxLgn))) return rc;
-    for (uint32_t c = 0; c < count; c++) {
-        if ((rc = ensure_tables(ctx, cws[c].field, s))) return rc;
-        if ((rc = ensure_fl(ctx, cws[c].field, lg2(cws[c].n), reinterpret_cast<uint32_t *>(ctx->scratch), s))) return rc;
-    }
+    if ((rc = validate_batch(op, cws, count))) return rc;
     Planner sizing{ctx};
     plan_batch(sizing, op, cws, count);
-    lch_batch *b = new (std::nothrow) lch_batch;
-    if (!b) return fail(LCH_ENOMEM, "host allocation failed");
-    b->ncw = count;
-    b->device = ctx->device;
-    b->counter_bytes = sizeof(BatchCounters) + sizeof(uint32_t) * std::max<uint32_t>(1, count);
-    auto dev_alloc = [&](void **p, size_t bytes) -> int {
-        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(LCH_ENOMEM, "batch allocation of %zu bytes failed", bytes);
-        }
-        return LCH_OK;
-    };
-    if ((rc = dev_alloc((void **)&b->scratch, sizing.scratch)) ||
-        (rc = dev_alloc((void **)&b->masks, sizing.masks.size() * 4)) ||
-        (rc = dev_alloc((void **)&b->ops, sizing.ops.size() * sizeof(BatchOp))) ||
-        (rc = dev_alloc((void **)&b->tasks, sizing.tasks.size() * sizeof(BatchTask))) ||
-        (rc = dev_alloc((void **)&b->counters, b->counter_bytes))) {
-        batch_free(b);
-        return rc;
-    }
-    Planner P{ctx, b->scratch, b->masks};
-    plan_batch(P, op, cws, count);
-    // stage-major queue, largest tasks first within a stage
-    std::stable_sort(P.tasks.begin(), P.tasks.end(), [](const PlanTask &x, const PlanTask &y) {
-        return x.stage != y.stage ? x.stage < y.stage : x.cost > y.cost;
-    });
-    // need = number of the codeword's tasks in earlier stages
-    std::vector<std::vector<uint32_t>> before(count);
-    for (const PlanTask &t : P.tasks) {
-        auto &v = before[t.cw];
-        if (v.size() <= t.stage) v.resize(t.stage + 1, 0);
-        v[t.stage]++;
-    }
-    for (auto &v : before) {
-        uint32_t acc = 0;
-        for (auto &x : v) {
-            const uint32_t here = x;
-            x = acc;
-            acc += here;
-        }
-    }
-    std::vector<BatchTask> tasks(P.tasks.size());
-    for (size_t i = 0; i < P.tasks.size(); i++) {
-        const PlanTask &t = P.tasks[i];
-        tasks[i] = {t.op, t.cw, before[t.cw][t.stage], t.g0, t.g1};
-    }
-    b->ntasks = (uint32_t)tasks.size();
-    auto upload = [&](void *dst, const void *src, size_t bytes) -> int {
-        if (bytes && cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
-            batch_free(b);
-            return cuda_fail(cudaGetLastError(), "batch upload");
-        }
-        return LCH_OK;
-    };
-    if ((rc = upload(b->masks, P.masks.data(), P.masks.size() * 4)) ||
-        (rc = upload(b->ops, P.ops.data(), P.ops.size() * sizeof(BatchOp))) ||
-        (rc = upload(b->tasks, tasks.data(), tasks.size() * sizeof(BatchTask))))
-        return rc;
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || sms < 1) sms = 1;
-    b->ctas = (uint32_t)sms; // one CTA per SM (the kernel uses ~192 KB of shared memory)
-    *out = b;
+    *bytes = batch_layout(sizing, count).total;
     return LCH_OK;
+}
+
+LCH_API int lch_batch_create_in(lch_ctx *ctx, int op, const lch_codeword *cws, uint32_t count, void *mem, size_t bytes,
+                                void *stream, lch_batch **out)
+{
+    if (!mem) return fail(LCH_EINVAL, "batch memory is NULL");
+    return batch_create(ctx, op, cws, count, static_cast<uint8_t *>(mem), bytes, (cudaStream_t)stream, out);
 }
 
 LCH_API int lch_batch_run(lch_ctx *ctx, lch_batch *b, void *stream)
@@ -762,6 +821,7 @@ LCH_API int lch_batch_run(lch_ctx *ctx, lch_batch *b, void *stream)
     if (!ctx || !b) return fail(LCH_EINVAL, "ctx or batch is NULL");
     DeviceScope ds(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
+    b->last = s;
     if (b->ntasks == 0) return LCH_OK;
     CU(cudaMemsetAsync(b->counters, 0, b->counter_bytes, s), "counter reset");
     BatchCounters *ctr = reinterpret_cast<BatchCounters *>(b->counters);
@@ -774,10 +834,11 @@ LCH_API int lch_batch_status(lch_ctx *ctx, lch_batch *b)
 {
     if (!ctx || !b) return fail(LCH_EINVAL, "ctx or batch is NULL");
     DeviceScope ds(ctx->device);
-    CU(cudaDeviceSynchronize(), "batch");
+    CU(cudaStreamSynchronize(b->last), "batch");
     if (b->ntasks == 0) return LCH_OK;
     BatchCounters h{};
-    CU(cudaMemcpy(&h, b->counters, sizeof(h), cudaMemcpyDeviceToHost), "batch status");
+    CU(cudaMemcpyAsync(&h, b->counters, sizeof(h), cudaMemcpyDeviceToHost, b->last), "batch status");
+    CU(cudaStreamSynchronize(b->last), "batch status");
     if (h.err) return fail(LCH_ECUDA, "a batch task gave up waiting for its predecessors");
     return LCH_OK;
 }
@@ -788,7 +849,7 @@ LCH_API void lch_batch_destroy(lch_batch *b)
 {
     if (!b) return;
     DeviceScope ds(b->device);
-    cudaDeviceSynchronize();
+    if (b->owned) cudaStreamSynchronize(b->last);
     batch_free(b);
 }
 

@@ -70,6 +70,8 @@ def load() -> ctypes.CDLL:
         "lch_derivative_noalloc": (i, [i, u32, vp, sz, vp]),
         "lch_batch_create": (i, [vp, i, vp, u32, ctypes.POINTER(vp)]),
         "lch_batch_run": (i, [vp, vp, vp]),
+        "lch_batch_bytes": (i, [vp, i, vp, u32, ctypes.POINTER(sz)]),
+        "lch_batch_create_in": (i, [vp, i, vp, u32, vp, sz, vp, ctypes.POINTER(vp)]),
         "lch_batch_status": (i, [vp, vp]),
         "lch_batch_tasks": (u32, [vp]),
         "lch_batch_destroy": (None, [vp]),
@@ -122,27 +124,43 @@ def derivative_noalloc(field: int, buf, stream=None):
     _check(load().lch_derivative_noalloc(field, buf.shape[0], p, S, _stream_handle(stream)))
 
 
+def _codeword_array(codewords, keep):
+    """ctypes array of struct lch_codeword; host masks are appended to `keep`."""
+    arr = (Codeword * max(1, len(codewords)))()
+    for i, (n, k, field, shards, mask) in enumerate(codewords):
+        p, S = _buf(shards, n)
+        m = None
+        if mask is not None:
+            m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).reshape(-1))
+            if m.size != n:
+                raise ValueError(f"codeword {i}: erasure mask must have n={n} entries")
+            keep.append(m)
+        arr[i] = Codeword(n, k, field, 0, S, p.value, None if m is None else m.ctypes.data)
+    return arr
+
+
 class Batch:
     """A planned batch of codewords (lch_batch_create); run() enqueues one
     persistent launch, status() waits and reports."""
 
-    def __init__(self, ctx, op, codewords):
-        """codewords: list of (n, k, field, shards_tensor, erasure_mask or None)."""
+    def __init__(self, ctx, op, codewords, mem=None, stream=None):
+        """codewords: list of (n, k, field, shards_tensor, erasure_mask or None).
+        mem: optional CUDA uint8 tensor holding the batch's device memory
+        (see batch_bytes); the batch then allocates nothing."""
         self._ctx = ctx
         self._keep = []
-        arr = (Codeword * max(1, len(codewords)))()
-        for i, (n, k, field, shards, mask) in enumerate(codewords):
-            p, S = _buf(shards, n)
-            m = None
-            if mask is not None:
-                m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).reshape(-1))
-                if m.size != n:
-                    raise ValueError(f"codeword {i}: erasure mask must have n={n} entries")
-                self._keep.append(m)
-            arr[i] = Codeword(n, k, field, 0, S, p.value, None if m is None else m.ctypes.data)
+        arr = self._array(codewords)
         h = ctypes.c_void_p()
-        _check(load().lch_batch_create(ctx._h, op, arr, len(codewords), ctypes.byref(h)))
+        if mem is None:
+            _check(load().lch_batch_create(ctx._h, op, arr, len(codewords), ctypes.byref(h)))
+        else:
+            self._keep.append(mem)
+            _check(load().lch_batch_create_in(ctx._h, op, arr, len(codewords), ctypes.c_void_p(mem.data_ptr()),
+                                              mem.numel(), _stream_handle(stream), ctypes.byref(h)))
         self._h = h
+
+    def _array(self, codewords):
+        return _codeword_array(codewords, self._keep)
 
     @property
     def tasks(self) -> int:
@@ -203,8 +221,16 @@ class Context:
                                        ctypes.byref(mu)))
         return {"launches": int(n.value), "ms": float(ms.value), "bytes": int(by.value), "mults": int(mu.value)}
 
-    def batch(self, op: int, codewords) -> "Batch":
-        return Batch(self, op, codewords)
+    def batch(self, op: int, codewords, mem=None, stream=None) -> "Batch":
+        return Batch(self, op, codewords, mem=mem, stream=stream)
+
+    def batch_bytes(self, op: int, codewords) -> int:
+        """Device bytes a batch of these codewords needs (lch_batch_bytes)."""
+        keep = []
+        arr = _codeword_array(codewords, keep)
+        out = ctypes.c_size_t()
+        _check(load().lch_batch_bytes(self._h, op, arr, len(codewords), ctypes.byref(out)))
+        return int(out.value)
 
     # Sec. III: Psi_h^l and its inverse, in place on h rows.
     def fft(self, field: int, l: int, buf, stream=None):

@@ -1,0 +1,91 @@
+"""The serving loop: host logic on the CPU (allocator, arrivals) and, on the
+GPU, that every request's result is the same alone and in the mix."""
+import numpy as np
+import pytest
+
+from paper_1404_3458_gb300 import lch
+from paper_1404_3458_gb300 import serve as SV
+from paper_1404_3458_gb300 import workloads as WL
+
+
+def test_arena_first_fit_and_merge():
+    a = SV.Arena(4096)
+    x = a.alloc(100)   # 256
+    y = a.alloc(1000)  # 1024
+    z = a.alloc(2816)  # the rest
+    assert (x, y, z) == (0, 256, 1280) and a.alloc(1) == -1
+    a.release(y, 1000)
+    assert a.alloc(2000) == -1 and a.alloc(512) == 256
+    a.release(x, 100)
+    a.release(256, 512)
+    a.release(z, 2816)
+    assert a.free == [(0, 4096)] and a.used == 0
+
+
+def test_poisson_arrivals():
+    t = SV.poisson_arrivals(1000.0, 20000, seed=3)
+    assert np.all(np.diff(t) > 0)
+    assert abs(t[-1] / 20000 - 1e-3) < 5e-5  # mean gap 1/rate
+
+
+def _requests(ctx, count, rate, seed):
+    import torch
+
+    g = np.random.default_rng(seed)
+    arr = SV.poisson_arrivals(rate, count, seed)
+    reqs, expect = [], []
+    for i in range(count):
+        n = int(g.choice([32, 64, 256, 1024]))
+        field = 8 if n <= 256 else 16
+        k = n * int(g.choice([2, 1, 3])) // 4
+        S = int(g.choice([64, 256, 1024]))
+        host = np.zeros((n, S), dtype=np.uint8)
+        host[:k] = WL.shards(k, S, seed=seed * 1000 + i)
+        dev = torch.from_numpy(host).cuda()
+        if g.random() < 0.7:
+            op, mask = lch.BATCH_ENCODE, None
+            alone = dev.clone()
+            ctx.rs_encode(n, k, field, alone)
+        else:
+            op = lch.BATCH_DECODE
+            ctx.rs_encode(n, k, field, dev)
+            mask = WL.erasure_mask(n, int(g.integers(0, n - k + 1)), seed=i)
+            alone = dev.clone()
+            dev[torch.from_numpy(mask.astype(bool)).cuda()] = 0xEE
+            tmp = dev.clone()
+            ctx.rs_decode(n, k, field, tmp, mask)
+            assert torch.equal(tmp, alone)
+        reqs.append(SV.Request(i, op, field, n, k, S, float(arr[i]), mask=mask, payload=dev))
+        expect.append(alone)
+    torch.cuda.synchronize()
+    return reqs, expect
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("budget_mb,rate", [(64, 20000.0), (8, 200000.0)])
+def test_served_results_equal_alone(ctx, budget_mb, rate):
+    import torch
+
+    reqs, expect = _requests(ctx, 60, rate, seed=budget_mb)
+    got = {}
+    server = SV.Server(ctx, budget_mb << 20, max_inflight=2, max_batch=32)
+    stats = server.run(reqs, on_done=lambda r: got.__setitem__(r.rid, r.buf.clone()))
+    torch.cuda.synchronize()
+    assert len(got) == len(reqs)
+    for r, e in zip(reqs, expect):
+        assert torch.equal(got[r.rid], e), (r.rid, r.op, r.n, r.k, r.shard_bytes)
+    assert stats["requests"] == 60 and stats["p99_ms"] >= stats["p50_ms"] > 0
+    # several requests were served by one launch (continuous batching)
+    assert stats["launch_groups"] < len(reqs)
+
+
+@pytest.mark.gpu
+def test_plain_loop_results_equal_alone(ctx):
+    import torch
+
+    reqs, expect = _requests(ctx, 24, 5000.0, seed=7)
+    got = {}
+    SV.serve_plain(ctx, reqs, 32 << 20, on_done=lambda r: got.__setitem__(r.rid, r.buf.clone()))
+    torch.cuda.synchronize()
+    for r, e in zip(reqs, expect):
+        assert torch.equal(got[r.rid], e)
