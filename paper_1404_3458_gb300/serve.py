@@ -98,6 +98,12 @@ def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
     return np.cumsum(g.exponential(1.0 / rate, size=count))
 
 
+def _estimate(r: Request) -> int:
+    """Device bytes a request may need while in flight: its buffer, batch
+    scratch (at most 2 n S for a decode) and its share of the task queue."""
+    return 3 * r.n * r.shard_bytes + 16 * r.n + 65536
+
+
 @dataclass
 class _Inflight:
     event: object
@@ -108,7 +114,7 @@ class _Inflight:
 
 
 class Server:
-    def __init__(self, ctx: "lch.Context", budget_bytes: int, max_inflight: int = 2, max_batch: int = 1024):
+    def __init__(self, ctx: "lch.Context", budget_bytes: int, max_inflight: int = 3, max_batch: int = 1024):
         import torch
 
         self.torch = torch
@@ -118,6 +124,10 @@ class Server:
         self.max_inflight = max_inflight
         self.max_batch = max_batch
         self.streams = [torch.cuda.Stream() for _ in range(max_inflight)]
+        # A lone request skips batch planning and runs as a single-codeword
+        # call; each launch slot has its own context so those calls never
+        # share context scratch across streams.
+        self.slot_ctx = [lch.Context(ctx.device) for _ in range(max_inflight)]
 
     def _view(self, off: int, n: int, S: int):
         return self.mem[off:off + n * S].view(n, S)
@@ -135,14 +145,36 @@ class Server:
         r.offset = -1
 
     def _plan(self, group: list, op: int, stream, f: "_Inflight") -> bool:
-        """Plan and launch one batch for `group`; False if its memory does not fit."""
+        """Launch `group` as one batch (a lone request as a single call);
+        False if its memory does not fit."""
+        if len(group) == 1:
+            r, c = group[0], self.slot_ctx[f.slot]
+            if op == lch.BATCH_ENCODE:
+                c.rs_encode(r.n, r.k, r.field, r.buf, stream=stream)
+            else:
+                c.rs_decode(r.n, r.k, r.field, r.buf, r.mask, stream=stream)
+            return True
         cws = [(r.n, r.k, r.field, r.buf, r.mask) for r in group]
-        nbytes = self.ctx.batch_bytes(op, cws)
+        # size the plan from the admission estimate; plan exactly only if short
+        nbytes = sum(_estimate(r) - r.n * r.shard_bytes for r in group)
         off = self.arena.alloc(nbytes)
-        if off < 0:
-            return False
+        if off >= 0:
+            try:
+                b = self.ctx.batch(op, cws, mem=self.mem[off:off + nbytes], stream=stream)
+            except lch.LchError as e:
+                self.arena.release(off, nbytes)
+                if e.status != lch.LCH_EINVAL:
+                    raise
+                b = None
+        else:
+            b = None
+        if b is None:
+            nbytes = self.ctx.batch_bytes(op, cws)
+            off = self.arena.alloc(nbytes)
+            if off < 0:
+                return False
+            b = self.ctx.batch(op, cws, mem=self.mem[off:off + nbytes], stream=stream)
         f.blocks.append((off, nbytes))
-        b = self.ctx.batch(op, cws, mem=self.mem[off:off + nbytes], stream=stream)
         b.run(stream)
         f.batches.append(b)
         return True
@@ -187,8 +219,15 @@ class Server:
                 slot = free_slots[-1]
                 stream = self.streams[slot]
                 admitted = []
-                while waiting and len(admitted) < self.max_batch and self._admit(waiting[0]):
+                room = self.arena.size - self.arena.used
+                while waiting and len(admitted) < self.max_batch:
+                    need = _estimate(waiting[0])
+                    if need > room or not self._admit(waiting[0]):
+                        break
+                    room -= need
                     admitted.append(waiting.popleft())
+                if not admitted and waiting and not inflight and _estimate(waiting[0]) > self.arena.size:
+                    raise RuntimeError("a request does not fit in the serving memory budget")
                 if admitted:
                     f = _Inflight(event=torch.cuda.Event(), slot=slot, batches=[], requests=[])
                     with torch.cuda.stream(stream):
@@ -200,11 +239,12 @@ class Server:
                         group = [r for r in admitted if r.op == op]
                         if not group:
                             continue
-                        if self._plan(group, op, stream, f):
-                            f.requests.extend(group)
-                            batches_launched += 1
-                        else:
-                            back.extend(group)
+                        while group:  # shrink the group from its tail until its plan fits
+                            if self._plan(group, op, stream, f):
+                                f.requests.extend(group)
+                                batches_launched += 1
+                                break
+                            back.append(group.pop())
                     if back:
                         stream.synchronize()  # their payload copies must finish before reuse
                     for r in back:  # keep arrival order at the head of the queue
