@@ -534,3 +534,51 @@ int orc_locator(int r, uint32_t n, const uint8_t *erased, uint32_t *pi)
     }
     return OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Polynomial multiplication in the basis (Sec. VI.A)                   */
+/* ------------------------------------------------------------------ */
+
+/* out (2h rows) = coefficients, in X_0..X_{2h-1}, of [a](x) * [b](x) where a
+ * and b hold h coefficients each (h = 2^lgh, 2h <= 2^r).  Plain definition:
+ * both factors are multiplied out in the monomial basis, the two coefficient
+ * vectors are convolved, and the product (degree <= 2h - 2) is converted back
+ * to the X basis by the triangular solve that deg X_i = i allows. */
+int orc_poly_mul(int r, int lgh, const uint16_t *a, const uint16_t *b, uint16_t *out, int64_t cols)
+{
+    const field_t *f = fld(r);
+    if (!f || lgh < 0 || lgh + 1 > r) return EINVAL_;
+    uint32_t h = 1u << lgh, h2 = 2 * h;
+    uint32_t *X = X_polys(f, lgh + 1);
+    uint32_t *pa = (uint32_t *)malloc(sizeof(uint32_t) * h);
+    uint32_t *pb = (uint32_t *)malloc(sizeof(uint32_t) * h);
+    uint32_t *pc = (uint32_t *)malloc(sizeof(uint32_t) * h2);
+    if (!X || !pa || !pb || !pc) { free(X); free(pa); free(pb); free(pc); return ENOMEM_; }
+    for (int64_t col = 0; col < cols; col++) {
+        for (uint32_t m = 0; m < h; m++) pa[m] = pb[m] = 0;
+        for (uint32_t i = 0; i < h; i++) {
+            const uint32_t *Xi = X + (uint64_t)i * (i + 1) / 2;
+            uint32_t da = a[(uint64_t)i * cols + col], db = b[(uint64_t)i * cols + col];
+            for (uint32_t m = 0; m <= i; m++) {
+                if (da) pa[m] ^= mul(f, da, Xi[m]);
+                if (db) pb[m] ^= mul(f, db, Xi[m]);
+            }
+        }
+        for (uint32_t m = 0; m < h2; m++) pc[m] = 0;
+        for (uint32_t i = 0; i < h; i++)
+            if (pa[i])
+                for (uint32_t j = 0; j < h; j++) pc[i + j] ^= mul(f, pa[i], pb[j]);
+        for (int64_t i = (int64_t)h2 - 1; i >= 0; i--) {
+            const uint32_t *Xi = X + (uint64_t)i * (i + 1) / 2;
+            uint32_t e = mul(f, pc[i], inv(f, Xi[i]));
+            out[(uint64_t)i * cols + col] = (uint16_t)e;
+            if (e)
+                for (int64_t m = 0; m <= i; m++) pc[m] ^= mul(f, e, Xi[m]);
+        }
+    }
+    free(X);
+    free(pa);
+    free(pb);
+    free(pc);
+    return OK;
+}

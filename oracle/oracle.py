@@ -26,7 +26,7 @@ _lib = None
 __all__ = [
     "build", "lib", "to_elems", "from_elems", "gf_mul", "gf_mul_bitwise", "gf_inv", "gf_exp",
     "gf_log", "gf_mul_vec", "W", "Wprime", "X", "W_poly", "X_poly", "fft", "ifft", "derivative",
-    "rs_encode", "rs_decode", "locator", "poly_eval",
+    "rs_encode", "rs_decode", "locator", "poly_eval", "poly_mul",
 ]
 
 
@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
             "orc_rs_encode": (ctypes.c_int, [ctypes.c_int, u32, u32, vp, i64, vp, i32]),
             "orc_rs_decode": (ctypes.c_int, [ctypes.c_int, u32, u32, vp, vp, i64, vp, i32]),
             "orc_locator": (ctypes.c_int, [ctypes.c_int, u32, vp, vp]),
+            "orc_poly_mul": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, vp, vp, i64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -248,4 +249,17 @@ def locator(r: int, n: int, erased: np.ndarray) -> np.ndarray:
     m = np.ascontiguousarray(erased, dtype=np.uint8)
     out = np.empty(n, dtype=np.uint32)
     _check(lib().orc_locator(r, n, _ptr(m), _ptr(out)), "locator")
+    return out
+
+
+def poly_mul(r: int, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Coefficients (2h rows, X basis) of the product of the polynomials with
+    X-basis coefficients a and b (h rows each), via the monomial basis."""
+    A = np.ascontiguousarray(a, dtype=np.uint16)
+    Bm = np.ascontiguousarray(b, dtype=np.uint16)
+    h, cols = A.shape
+    lgh = h.bit_length() - 1
+    assert 1 << lgh == h and Bm.shape == A.shape
+    out = np.empty((2 * h, cols), dtype=np.uint16)
+    _check(lib().orc_poly_mul(r, lgh, _ptr(A), _ptr(Bm), _ptr(out), cols), "poly_mul")
     return out
