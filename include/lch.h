@@ -106,6 +106,15 @@ LCH_API int lch_derivative(lch_ctx *ctx, int field, uint32_t h, void *buf, size_
  * Argument rules, layout and errors are otherwise those of lch_derivative. */
 LCH_API int lch_derivative_noalloc(int field, uint32_t h, void *buf, size_t shard_bytes, void *stream);
 
+/* Product of two polynomials in the basis (Sec. VI.A): with a and b holding
+ * the h coefficients of [A_h] and [B_h] (h rows each), c (2h rows) receives
+ * the 2h coefficients of [A_h](x) [B_h](x), computed as
+ * (Psi_2h^0)^-1 [Psi_2h^0[A_2h] * Psi_2h^0[B_2h]] with A_2h, B_2h the inputs
+ * padded with h zero rows.  h: power of two, 1 <= h <= 2^(r-1).  a, b and c
+ * must not overlap.  Uses context scratch of 2 h shard_bytes bytes. */
+LCH_API int lch_poly_mul(lch_ctx *ctx, int field, uint32_t h, const void *a, const void *b, void *c,
+                         size_t shard_bytes, void *stream);
+
 /* Systematic (n, k) Reed-Solomon encoding (Sec. V, Algorithm 1).
  * shards holds n rows; rows 0..k-1 are the message m_0..m_{k-1} and are only
  * read; rows k..n-1 are overwritten with F(w_k)..F(w_{n-1}), where F is the

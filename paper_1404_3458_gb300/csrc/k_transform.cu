@@ -13,6 +13,8 @@
 // spans a slice of the shard columns; the factor records of its 2^nlev - 1
 // butterfly blocks are staged in shared memory once per CTA and reused for all
 // the column slices the CTA walks.
+#include <algorithm>
+
 #include "lch_internal.cuh"
 
 namespace lch {
@@ -800,7 +802,47 @@ __global__ void __launch_bounds__(kPassThreads, 1)
     }
 }
 
+// c = c (.) t elementwise (both operands vary): a * b = alpha^(log a + log b).
+template <int R>
+__global__ void __launch_bounds__(kThreads)
+    k_pointwise(uint8_t *c, const uint8_t *t, size_t bytes, const uint16_t *__restrict__ logt,
+                const uint16_t *__restrict__ expt)
+{
+    constexpr uint32_t M = (1u << R) - 1, E = R / 8, PER = 4 / E;
+    const size_t words = bytes / 4;
+    uint32_t *cw = reinterpret_cast<uint32_t *>(c);
+    const uint32_t *tw = reinterpret_cast<const uint32_t *>(t);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < words; i += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t x = cw[i], y = tw[i];
+        uint32_t r = 0;
+#pragma unroll
+        for (uint32_t e = 0; e < PER; e++) {
+            const uint32_t sh = e * R, mask = (1u << R) - 1;
+            const uint32_t a = (x >> sh) & mask, b = (y >> sh) & mask;
+            if (a && b) {
+                uint32_t s = (uint32_t)__ldg(logt + a) + __ldg(logt + b);
+                s = s >= M ? s - M : s;
+                r |= (uint32_t)__ldg(expt + s) << sh;
+            }
+        }
+        cw[i] = r;
+    }
+}
+
 } // namespace
+
+cudaError_t launch_pointwise(int r, uint8_t *c, const uint8_t *t, size_t bytes, const FieldTables &tab,
+                             cudaStream_t s, uint64_t *launches)
+{
+    const size_t words = bytes / 4;
+    const unsigned blocks = (unsigned)std::min<size_t>((words + kThreads - 1) / kThreads, (size_t)kSms * 16);
+    if (r == 8)
+        k_pointwise<8><<<blocks, kThreads, 0, s>>>(c, t, bytes, tab.logt, tab.expt);
+    else
+        k_pointwise<16><<<blocks, kThreads, 0, s>>>(c, t, bytes, tab.logt, tab.expt);
+    *launches += 1;
+    return cudaGetLastError();
+}
 
 cudaError_t configure_transform_kernels()
 {

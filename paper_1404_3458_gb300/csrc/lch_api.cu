@@ -766,6 +766,39 @@ LCH_API int lch_derivative(lch_ctx *ctx, int field, uint32_t h, void *buf, size_
     return derivative(ctx, field, h, p, p, ctx->scratch, shard_bytes, s);
 }
 
+LCH_API int lch_poly_mul(lch_ctx *ctx, int field, uint32_t h, const void *a, const void *b, void *c,
+                         size_t shard_bytes, void *stream)
+{
+    int rc;
+    if ((rc = check_field(field)) || (rc = check_len("h", h, field)) || (rc = check_buffer(a, h, shard_bytes)) ||
+        (rc = check_buffer(b, h, shard_bytes)) || (rc = check_buffer(c, 2ull * h, shard_bytes)))
+        return rc;
+    if (2ull * h > (1ull << field)) return fail(LCH_EINVAL, "h must be at most 2^(r-1), got %u", h);
+    const size_t S = shard_bytes, half = (size_t)h * S;
+    auto overlap = [](const void *p, size_t pn, const void *q, size_t qn) {
+        const uint8_t *x = (const uint8_t *)p, *y = (const uint8_t *)q;
+        return x < y + qn && y < x + pn;
+    };
+    if (overlap(c, 2 * half, a, half) || overlap(c, 2 * half, b, half)) return fail(LCH_EINVAL, "c must not overlap a or b");
+    if (!ctx) return fail(LCH_EINVAL, "ctx is NULL");
+    DeviceScope ds(ctx->device);
+    if (!ds.ok) return fail(LCH_ECUDA, "cannot select device %d", ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ensure_tables(ctx, field, s))) return rc;
+    if ((rc = ensure_scratch(ctx, 2 * half))) return rc;
+    uint8_t *C = static_cast<uint8_t *>(c), *T = ctx->scratch;
+    // zero-padded operands (A_2h, B_2h)
+    CU(cudaMemcpyAsync(C, a, half, cudaMemcpyDeviceToDevice, s), "copy");
+    CU(cudaMemsetAsync(C + half, 0, half, s), "memset");
+    CU(cudaMemcpyAsync(T, b, half, cudaMemcpyDeviceToDevice, s), "copy");
+    CU(cudaMemsetAsync(T + half, 0, half, s), "memset");
+    if ((rc = transform(ctx, field, 2 * h, 0, 0, C, C, S, s))) return rc;
+    if ((rc = transform(ctx, field, 2 * h, 0, 0, T, T, S, s))) return rc;
+    PROFM(LCH_KIND_ROWSCALE, 3 * (2 * half), 2 * half / (field / 8),
+          launch_pointwise(field, C, T, 2 * half, ctx->tab[field == LCH_GF16], s, &ctx->launches));
+    return transform(ctx, field, 2 * h, 0, 1, C, C, S, s);
+}
+
 LCH_API int rs_encode(lch_ctx *ctx, uint32_t n, uint32_t k, int field, void *shards, size_t shard_bytes, void *stream)
 {
     int rc;

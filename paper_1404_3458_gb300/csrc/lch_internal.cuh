@@ -188,6 +188,10 @@ struct DerivArgs {
 };
 cudaError_t launch_deriv(int r, int mode, const DerivArgs &a, cudaStream_t s, uint64_t *launches);
 
+// c = c (.) t elementwise over `bytes` bytes (Sec. VI.A pointwise product).
+cudaError_t launch_pointwise(int r, uint8_t *c, const uint8_t *t, size_t bytes, const FieldTables &tab,
+                             cudaStream_t s, uint64_t *launches);
+
 // dst[t] = src[t] * coef[t] for t < rows (a zero coefficient zeroes the row);
 // with skip_zero, rows whose coefficient is zero are left untouched.
 cudaError_t launch_rowscale(int r, uint8_t *dst, const uint8_t *src, size_t S, uint32_t rows,

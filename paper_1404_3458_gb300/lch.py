@@ -68,6 +68,7 @@ def load() -> ctypes.CDLL:
         "lch_last_error": (ctypes.c_char_p, []),
         "lch_launch_count": (ctypes.c_uint64, [vp]),
         "lch_derivative_noalloc": (i, [i, u32, vp, sz, vp]),
+        "lch_poly_mul": (i, [vp, i, u32, vp, vp, vp, sz, vp]),
         "lch_batch_create": (i, [vp, i, vp, u32, ctypes.POINTER(vp)]),
         "lch_batch_run": (i, [vp, vp, vp]),
         "lch_batch_bytes": (i, [vp, i, vp, u32, ctypes.POINTER(sz)]),
@@ -245,6 +246,13 @@ class Context:
     def derivative(self, field: int, buf, stream=None):
         p, S = _buf(buf)
         _check(load().lch_derivative(self._h, field, buf.shape[0], p, S, _stream_handle(stream)))
+
+    # Sec. VI.A: c (2h rows) = coefficients of [a](x) [b](x); a, b: h rows.
+    def poly_mul(self, field: int, a, b, c, stream=None):
+        pa, S = _buf(a)
+        pb, _ = _buf(b, a.shape[0])
+        pc, _ = _buf(c, 2 * a.shape[0])
+        _check(load().lch_poly_mul(self._h, field, a.shape[0], pa, pb, pc, S, _stream_handle(stream)))
 
     # Sec. V, Algorithm 1.
     def rs_encode(self, n: int, k: int, field: int, shards, stream=None):
