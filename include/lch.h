@@ -235,6 +235,42 @@ LCH_API int lch_profile_enable(lch_ctx *ctx, int on);
 LCH_API int lch_profile_read(lch_ctx *ctx, int kind, uint64_t *launches, double *total_ms, uint64_t *bytes,
                              uint64_t *mults);
 
+/* ---- Autotuning of the transform passes (the paper has no counterpart) ---
+ * An h-point transform runs its lg h butterfly levels (Sec. III.C/E) in one
+ * pass (lg h <= 8) or two: the low pass takes levels [0, split), the high pass
+ * levels [split, lg h); each pass walks the shards in column tiles of
+ * 2^lg_tile bytes.  The result never depends on the plan, only the speed.
+ * A plan holds for one (field, h, shard_bytes) on the context that tuned or
+ * received it and is used by lch_fft, lch_ifft, rs_encode, rs_decode,
+ * lch_poly_mul and batches planned afterwards (lch_derivative keeps its own
+ * passes). */
+typedef struct lch_tuning {
+    uint32_t split;        /* levels of the low pass; lg h when there is one pass */
+    uint32_t lg_tile_low;  /* log2 column-tile bytes of the low pass, 4..12 */
+    uint32_t lg_tile_high; /* ... of the high pass; 0 when there is one pass */
+    float ms;              /* lch_autotune: device ms of one Psi plus one Psi^-1 */
+} lch_tuning;
+
+/* Time candidate plans for (field, h, shard_bytes) on `stream` and keep the
+ * fastest on the context; *best receives it.  Candidates: the splits with
+ * both passes <= 8 levels among {ceil(lg h/2), floor(lg h/2), lg h-8, 8}, and
+ * for each pass the default tile width and its two neighbours that fit in
+ * shared memory.  Each pass is timed with CUDA events, forward and inverse,
+ * after one warm-up, on h * shard_bytes bytes of context scratch filled with a
+ * fixed pattern (grown by cudaMalloc if needed; no caller data is touched).
+ * Synchronises `stream`.  Errors: LCH_EINVAL (bad field, h not a power of two
+ * in [2, 2^field], shard_bytes zero or not a multiple of 16, NULL pointer),
+ * LCH_ENOMEM, LCH_ECUDA. */
+LCH_API int lch_autotune(lch_ctx *ctx, int field, uint32_t h, size_t shard_bytes, void *stream, lch_tuning *best);
+
+/* Install a plan for (field, h, shard_bytes), e.g. one read from a cache of
+ * earlier lch_autotune results; plan NULL removes it (defaults again).  The
+ * plan is checked (split, both passes <= 8 levels, widths in 4..12 and within
+ * shared memory for these sizes); LCH_EINVAL if it is not valid, nothing
+ * changed.  Not synchronised with work in flight: set plans before the calls
+ * that should use them. */
+LCH_API int lch_tune_set(lch_ctx *ctx, int field, uint32_t h, size_t shard_bytes, const lch_tuning *plan);
+
 #ifdef __cplusplus
 }
 #endif

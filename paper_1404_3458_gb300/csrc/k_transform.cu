@@ -646,7 +646,7 @@ template <int R, int INV>
 cudaError_t pass_impl(const PassArgs &a, cudaStream_t s)
 {
     const uint32_t nrows = 1u << a.nlev;
-    const uint32_t lg_cw = pick_lg_cw(nrows, a.S);
+    const uint32_t lg_cw = a.lg_cw ? a.lg_cw : pick_lg_cw(nrows, a.S);
     const size_t smem = tab_bytes<R>(nrows - 1) + (2 * (size_t)nrows << lg_cw);
     const uint32_t ngroups = a.h >> a.nlev;
     const size_t ntiles = (a.S + (1ull << lg_cw) - 1) >> lg_cw;
@@ -864,6 +864,42 @@ cudaError_t configure_transform_kernels()
 }
 
 uint32_t plan_lg_cw(uint32_t nrows, size_t S) { return pick_lg_cw(nrows, S); }
+
+uint32_t max_lg_cw(int r, uint32_t nlev, size_t S)
+{
+    const size_t budget = 220 * 1024;
+    const size_t tab = r == 16 ? tab_bytes<16>((1u << nlev) - 1) : tab_bytes<8>((1u << nlev) - 1);
+    uint32_t lg = 4;
+    while (lg < 12 && tab + (2ull << nlev << (lg + 1)) <= budget && (1ull << (lg + 1)) < 2 * S) lg++;
+    return lg;
+}
+
+uint32_t batch_max_lg_cw(int r, uint32_t nlev)
+{
+    const size_t tab = r == 16 ? tab_bytes<16>((1u << nlev) - 1) : tab_bytes<8>((1u << nlev) - 1);
+    uint32_t lg = 4;
+    while (lg < 12 && tab + (2ull << nlev << (lg + 1)) <= batch_body_smem()) lg++;
+    return lg;
+}
+
+namespace {
+__global__ void k_fill(uint32_t *p, size_t words)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < words; i += (size_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)i * 2654435761u + 0x9E3779B9u;
+        x ^= x >> 15;
+        x *= 2246822519u;
+        x ^= x >> 13;
+        p[i] = x;
+    }
+}
+} // namespace
+
+cudaError_t launch_fill(uint8_t *p, size_t bytes, cudaStream_t s)
+{
+    k_fill<<<kSms * 4, kThreads, 0, s>>>(reinterpret_cast<uint32_t *>(p), bytes / 4);
+    return cudaGetLastError();
+}
 
 size_t batch_smem_bytes() { return batch_body_smem() + 16; } // + the queue control words
 

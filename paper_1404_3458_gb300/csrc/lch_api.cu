@@ -5,7 +5,9 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "../../include/lch.h"
@@ -29,6 +31,17 @@ struct lch_ctx {
     bool prof_on = false;
     std::vector<Rec> prof;
     size_t prof_used = 0;
+    // autotuned pass plans per (field, lg h, shard bytes): levels of the low
+    // pass and the log2 column-tile width of each pass
+    struct Plan {
+        uint32_t a;
+        uint32_t lg[2];
+    };
+    std::map<std::tuple<int, uint32_t, size_t>, Plan> tuned;
+    // locator of the shortened code per (field, n, k): the erasure set is
+    // always {k..n-1}, so Pi(j) (j < k, zero above) and 1/Pi'(j) (j >= k)
+    // are computed once; 2n uint16 per entry (pre, then post)
+    std::map<std::tuple<int, uint32_t, uint32_t>, uint16_t *> shortened;
 };
 
 namespace {
@@ -189,7 +202,45 @@ void split_levels(uint32_t lgh, uint32_t *a, uint32_t *b)
     }
 }
 
-// h-point transform (inverse != 0: (Psi_h^l)^-1) from src to dst.
+// Level split and tile widths of an h-point transform: the autotuned plan when
+// there is one, else the defaults (balanced split, ~32 KB tiles).
+void pass_plan(const lch_ctx *ctx, int field, uint32_t lgh, size_t S, uint32_t *a, uint32_t *b, uint32_t lg[2])
+{
+    auto it = ctx->tuned.find(std::make_tuple(field, lgh, S));
+    if (it != ctx->tuned.end()) {
+        *a = it->second.a;
+        *b = lgh - *a;
+        lg[0] = it->second.lg[0];
+        lg[1] = it->second.lg[1];
+        return;
+    }
+    split_levels(lgh, a, b);
+    lg[0] = plan_lg_cw(1u << *a, S);
+    lg[1] = *b ? plan_lg_cw(1u << *b, S) : 0;
+}
+
+// One pass over levels [L0, L0 + nlev); `lg_cw` 0 = default tile width.
+int run_pass(lch_ctx *ctx, int field, uint32_t h, uint32_t l, int inverse, const uint8_t *src, uint8_t *dst, size_t S,
+             uint32_t L0, uint32_t nlev, uint32_t lg_cw, cudaStream_t s)
+{
+    PassArgs p;
+    p.S = S;
+    p.h = h;
+    p.l = l;
+    p.inverse = inverse;
+    p.rec = ctx->tab[field == LCH_GF16].rec;
+    p.src = src;
+    p.dst = dst;
+    p.L0 = L0;
+    p.nlev = nlev;
+    p.lg_cw = lg_cw;
+    const uint64_t cols = S / (field / 8);
+    PROFM(LCH_KIND_PASS, 2ull * h * S, (uint64_t)(h / 2) * cols * nlev, launch_pass(field, p, s, &ctx->launches));
+    return LCH_OK;
+}
+
+// h-point transform (inverse != 0: (Psi_h^l)^-1) from src to dst.  Psi^-1
+// runs the low levels first, Psi the high levels first.
 int transform(lch_ctx *ctx, int field, uint32_t h, uint32_t l, int inverse, const uint8_t *src, uint8_t *dst,
               size_t S, cudaStream_t s)
 {
@@ -198,33 +249,83 @@ int transform(lch_ctx *ctx, int field, uint32_t h, uint32_t l, int inverse, cons
         if (src != dst) CU(cudaMemcpyAsync(dst, src, S, cudaMemcpyDeviceToDevice, s), "copy");
         return LCH_OK;
     }
-    uint32_t a, b;
-    split_levels(lgh, &a, &b);
-    PassArgs p;
-    p.S = S;
-    p.h = h;
-    p.l = l;
-    p.inverse = inverse;
-    p.rec = ctx->tab[field == LCH_GF16].rec;
-    // (Psi)^-1 runs the low levels first, Psi the high levels first.
-    uint32_t first_L0 = inverse ? 0 : a, first_n = inverse ? a : b;
-    uint32_t second_L0 = inverse ? a : 0, second_n = inverse ? b : a;
-    if (b == 0) {
-        first_L0 = 0;
-        first_n = a;
+    uint32_t a, b, lg[2];
+    pass_plan(ctx, field, lgh, S, &a, &b, lg);
+    int rc;
+    if (b == 0) return run_pass(ctx, field, h, l, inverse, src, dst, S, 0, a, lg[0], s);
+    if (inverse) {
+        if ((rc = run_pass(ctx, field, h, l, 1, src, dst, S, 0, a, lg[0], s))) return rc;
+        return run_pass(ctx, field, h, l, 1, dst, dst, S, a, b, lg[1], s);
     }
-    const uint64_t bytes = 2ull * h * S;
-    const uint64_t cols = S / (field / 8), per_level = (uint64_t)(h / 2) * cols;
-    p.src = src;
-    p.dst = dst;
-    p.L0 = first_L0;
-    p.nlev = first_n;
-    PROFM(LCH_KIND_PASS, bytes, per_level * first_n, launch_pass(field, p, s, &ctx->launches));
-    if (b) {
-        p.src = dst;
-        p.L0 = second_L0;
-        p.nlev = second_n;
-        PROFM(LCH_KIND_PASS, bytes, per_level * second_n, launch_pass(field, p, s, &ctx->launches));
+    if ((rc = run_pass(ctx, field, h, l, 0, src, dst, S, a, b, lg[1], s))) return rc;
+    return run_pass(ctx, field, h, l, 0, dst, dst, S, 0, a, lg[0], s);
+}
+
+// Candidate level splits of an autotuned lg h-level transform: every listed
+// split whose two passes both have 1..8 levels (one pass when lg h <= 8).
+int tune_splits(uint32_t lgh, uint32_t out[4])
+{
+    if (lgh <= 8) {
+        out[0] = lgh;
+        return 1;
+    }
+    const uint32_t cand[4] = {(lgh + 1) / 2, lgh / 2, lgh - 8, 8};
+    int n = 0;
+    for (uint32_t a : cand) {
+        if (a < 1 || a > 8 || lgh - a < 1 || lgh - a > 8) continue;
+        bool seen = false;
+        for (int i = 0; i < n; i++) seen |= out[i] == a;
+        if (!seen) out[n++] = a;
+    }
+    return n;
+}
+
+struct EventPair {
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    bool ok = false;
+    EventPair() { ok = cudaEventCreate(&e[0]) == cudaSuccess && cudaEventCreate(&e[1]) == cudaSuccess; }
+    ~EventPair()
+    {
+        for (cudaEvent_t x : e)
+            if (x) cudaEventDestroy(x);
+    }
+};
+
+// Device ms of one forward plus one inverse run of the pass over levels
+// [L0, L0 + nlev) with column tiles of 2^lg_cw bytes, on buf in place (mean
+// of three runs after one warm-up).
+int time_pass(lch_ctx *ctx, int field, uint32_t h, uint8_t *buf, size_t S, uint32_t L0, uint32_t nlev, uint32_t lg_cw,
+              EventPair &ev, cudaStream_t s, float *ms)
+{
+    const int reps = 3;
+    int rc;
+    for (int it = 0; it <= reps; it++) {
+        if (it == 1) CU(cudaEventRecord(ev.e[0], s), "cudaEventRecord");
+        if ((rc = run_pass(ctx, field, h, 0, 0, buf, buf, S, L0, nlev, lg_cw, s))) return rc;
+        if ((rc = run_pass(ctx, field, h, 0, 1, buf, buf, S, L0, nlev, lg_cw, s))) return rc;
+    }
+    CU(cudaEventRecord(ev.e[1], s), "cudaEventRecord");
+    CU(cudaEventSynchronize(ev.e[1]), "cudaEventSynchronize");
+    float t = 0;
+    CU(cudaEventElapsedTime(&t, ev.e[0], ev.e[1]), "cudaEventElapsedTime");
+    *ms = t / reps;
+    return LCH_OK;
+}
+
+// Fastest tile width for one pass among the default and its neighbours.
+int tune_pass(lch_ctx *ctx, int field, uint32_t h, uint8_t *buf, size_t S, uint32_t L0, uint32_t nlev, EventPair &ev,
+              cudaStream_t s, uint32_t *best_lg, float *best_ms)
+{
+    const uint32_t def = plan_lg_cw(1u << nlev, S), hi = max_lg_cw(field, nlev, S);
+    *best_ms = -1.f;
+    for (uint32_t lg = def > 4 ? def - 1 : 4; lg <= def + 1 && lg <= hi; lg++) {
+        float ms = 0;
+        int rc = time_pass(ctx, field, h, buf, S, L0, nlev, lg, ev, s, &ms);
+        if (rc) return rc;
+        if (*best_ms < 0 || ms < *best_ms) {
+            *best_ms = ms;
+            *best_lg = lg;
+        }
     }
     return LCH_OK;
 }
@@ -258,8 +359,48 @@ int derivative(lch_ctx *ctx, int field, uint32_t h, const uint8_t *src, uint8_t 
     return LCH_OK;
 }
 
+// Pi(j) off E and 1/Pi'(j) on E for E = {k..n-1} (the shortened code's
+// parity rows), cached on the context: the erasure set of an encode-by-decode
+// depends only on (n, k).
+int ensure_shortened(lch_ctx *ctx, int field, uint32_t n, uint32_t k, cudaStream_t s, const uint16_t **out)
+{
+    const auto key = std::make_tuple(field, n, k);
+    auto it = ctx->shortened.find(key);
+    if (it != ctx->shortened.end()) {
+        *out = it->second;
+        return LCH_OK;
+    }
+    int rc;
+    if ((rc = ensure_tables(ctx, field, s))) return rc;
+    if ((rc = ensure_scratch(ctx, sizeof(uint32_t) * (size_t)n))) return rc;
+    uint32_t *work = reinterpret_cast<uint32_t *>(ctx->scratch);
+    const uint32_t lgn = lg2(n);
+    if ((rc = ensure_fl(ctx, field, lgn, work, s))) return rc;
+    uint16_t *loc = nullptr;
+    if (cudaMalloc(&loc, sizeof(uint16_t) * 2 * (size_t)n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LCH_ENOMEM, "allocation of the shortened-code locator failed");
+    }
+    MaskBits bits;
+    memset(&bits, 0, sizeof(bits));
+    for (uint32_t j = k; j < n; j++) bits.w[j >> 5] |= 1u << (j & 31);
+    cudaError_t e = launch_locator(field, ctx->tab[field == LCH_GF16], lgn, bits, ctx->fl[field == LCH_GF16][lgn], work,
+                                   loc, loc + n, s, &ctx->launches);
+    // later calls may come on other streams (and reuse the work scratch)
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(loc);
+        return cuda_fail(e, "shortened-code locator");
+    }
+    ctx->shortened[key] = loc;
+    *out = loc;
+    return LCH_OK;
+}
+
+// Algorithm 2 on the rows flagged in `mask`.  `loc` (optional) holds Pi and
+// 1/Pi' for exactly this erasure set (2n uint16); the locator is then skipped.
 int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards, size_t S, const uint8_t *mask,
-                cudaStream_t s)
+                cudaStream_t s, const uint16_t *loc = nullptr)
 {
     const uint32_t lgn = lg2(n);
     MaskBits bits;
@@ -281,14 +422,22 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
     rc = ensure_scratch(ctx, off_work + align_up(sizeof(uint32_t) * n));
     if (rc) return rc;
     uint8_t *phi = ctx->scratch, *phi2 = ctx->scratch + off_phi2;
-    uint16_t *pre = reinterpret_cast<uint16_t *>(ctx->scratch + off_pre);
-    uint16_t *post = reinterpret_cast<uint16_t *>(ctx->scratch + off_post);
-    uint32_t *work = reinterpret_cast<uint32_t *>(ctx->scratch + off_work);
-    rc = ensure_fl(ctx, field, lgn, work, s);
-    if (rc) return rc;
-    const FieldTables &t = ctx->tab[field == LCH_GF16];
-    // Step 1: Pi(j) off E and 1/Pi'(j) on E.
-    PROF(LCH_KIND_LOCATOR, 0, launch_locator(field, t, lgn, bits, ctx->fl[field == LCH_GF16][lgn], work, pre, post, s, &ctx->launches));
+    const uint16_t *pre = reinterpret_cast<uint16_t *>(ctx->scratch + off_pre);
+    const uint16_t *post = reinterpret_cast<uint16_t *>(ctx->scratch + off_post);
+    if (loc) {
+        pre = loc;
+        post = loc + n;
+    } else {
+        uint16_t *wpre = reinterpret_cast<uint16_t *>(ctx->scratch + off_pre);
+        uint16_t *wpost = reinterpret_cast<uint16_t *>(ctx->scratch + off_post);
+        uint32_t *work = reinterpret_cast<uint32_t *>(ctx->scratch + off_work);
+        rc = ensure_fl(ctx, field, lgn, work, s);
+        if (rc) return rc;
+        const FieldTables &t = ctx->tab[field == LCH_GF16];
+        // Step 1: Pi(j) off E and 1/Pi'(j) on E.
+        PROF(LCH_KIND_LOCATOR, 0,
+             launch_locator(field, t, lgn, bits, ctx->fl[field == LCH_GF16][lgn], work, wpre, wpost, s, &ctx->launches));
+    }
     // Step 2: Phi = F * Pi, zero on erased rows (eq. hatF(l)).
     const uint64_t cols = S / (field / 8);
     PROFM(LCH_KIND_ROWSCALE, (uint64_t)(n - ne) * S + (uint64_t)n * S, (uint64_t)(n - ne) * cols,
@@ -312,13 +461,14 @@ int encode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
 {
     if (k == n) return LCH_OK;
     if (!is_pow2(k)) {
-        // Shortened code: recover rows k..n-1 as erasures (same unique F).
-        uint8_t *mask = new uint8_t[n];
-        memset(mask, 0, k);
-        memset(mask + k, 1, n - k);
-        int rc = decode_impl(ctx, n, k, field, shards, S, mask, s);
-        delete[] mask;
-        return rc;
+        // Shortened code: recover rows k..n-1 as erasures (same unique F),
+        // with the locator of that fixed erasure set cached per (n, k).
+        const uint16_t *loc = nullptr;
+        int rc = ensure_shortened(ctx, field, n, k, s, &loc);
+        if (rc) return rc;
+        std::vector<uint8_t> mask(n, 0);
+        std::fill(mask.begin() + k, mask.end(), 1);
+        return decode_impl(ctx, n, k, field, shards, S, mask.data(), s, loc);
     }
     int rc = ensure_tables(ctx, field, s);
     if (rc) return rc;
@@ -377,23 +527,25 @@ struct Planner {
         }
     }
     // Transform passes of an h-point transform as in transform(); returns the
-    // next free stage.
+    // next free stage.  Tile widths are capped to the batch kernel's shared memory.
     uint32_t add_transform(uint32_t stage, uint32_t cw, int field, uint32_t h, uint32_t l, int inverse,
                            const uint8_t *src, uint8_t *dst, size_t S)
     {
-        uint32_t a, b;
-        split_levels(lg2(h), &a, &b);
+        uint32_t a, b, lg[2];
+        pass_plan(ctx, field, lg2(h), S, &a, &b, lg);
         uint32_t L0[2] = {inverse ? 0u : a, inverse ? a : 0u}, nl[2] = {inverse ? a : b, inverse ? b : a};
+        uint32_t lgs[2] = {inverse ? lg[0] : lg[1], inverse ? lg[1] : lg[0]};
         if (b == 0) {
             L0[0] = 0;
             nl[0] = a;
+            lgs[0] = lg[0];
         }
         for (int p = 0; p < (b ? 2 : 1); p++) {
             BatchOp op{};
             op.type = kOpPass;
             op.field = field;
             op.mode = inverse;
-            op.lg_cw = plan_lg_cw(1u << nl[p], S);
+            op.lg_cw = std::min(lgs[p], batch_max_lg_cw(field, nl[p]));
             op.src = p == 0 ? src : dst;
             op.dst = dst;
             op.S = S;
@@ -408,29 +560,37 @@ struct Planner {
     }
 };
 
-void plan_decode(Planner &P, uint32_t cw, uint32_t n, int field, uint8_t *shards, size_t S, const uint8_t *mask)
+// Algorithm 2 for one codeword.  `cached` (optional): Pi and 1/Pi' of this
+// erasure set computed earlier (2n uint16); the locator stage is then left out.
+void plan_decode(Planner &P, uint32_t cw, uint32_t n, int field, uint8_t *shards, size_t S, const uint8_t *mask,
+                 const uint16_t *cached = nullptr)
 {
     const uint32_t lgn = lg2(n);
     const FieldTables &t = P.ctx->tab[field == LCH_GF16];
     uint8_t *phi = P.reserve((size_t)n * S), *phi2 = P.reserve((size_t)n * S);
-    uint16_t *pre = reinterpret_cast<uint16_t *>(P.reserve(sizeof(uint16_t) * n));
-    uint16_t *post = reinterpret_cast<uint16_t *>(P.reserve(sizeof(uint16_t) * n));
-    const size_t moff = P.masks.size();
-    P.masks.resize(moff + ((n + 31) / 32), 0u);
-    for (uint32_t j = 0; j < n; j++)
-        if (mask[j]) P.masks[moff + (j >> 5)] |= 1u << (j & 31);
+    const uint16_t *pre = cached, *post = cached ? cached + n : nullptr;
     uint32_t stage = 0;
-    BatchOp loc{};
-    loc.type = kOpLocator;
-    loc.field = field;
-    loc.L0 = lgn;
-    loc.h = n;
-    loc.tab0 = reinterpret_cast<const uint8_t *>(P.ctx->fl[field == LCH_GF16][lgn]);
-    loc.tab1 = reinterpret_cast<const uint8_t *>(t.expt);
-    loc.mask = P.mask_base + moff;
-    loc.pre = pre;
-    loc.post = post;
-    P.tasks.push_back({stage++, P.add_op(loc), cw, 0, 1, (uint64_t)n * 64});
+    if (!cached) {
+        uint16_t *wpre = reinterpret_cast<uint16_t *>(P.reserve(sizeof(uint16_t) * n));
+        uint16_t *wpost = reinterpret_cast<uint16_t *>(P.reserve(sizeof(uint16_t) * n));
+        const size_t moff = P.masks.size();
+        P.masks.resize(moff + ((n + 31) / 32), 0u);
+        for (uint32_t j = 0; j < n; j++)
+            if (mask[j]) P.masks[moff + (j >> 5)] |= 1u << (j & 31);
+        BatchOp loc{};
+        loc.type = kOpLocator;
+        loc.field = field;
+        loc.L0 = lgn;
+        loc.h = n;
+        loc.tab0 = reinterpret_cast<const uint8_t *>(P.ctx->fl[field == LCH_GF16][lgn]);
+        loc.tab1 = reinterpret_cast<const uint8_t *>(t.expt);
+        loc.mask = P.mask_base + moff;
+        loc.pre = wpre;
+        loc.post = wpost;
+        P.tasks.push_back({stage++, P.add_op(loc), cw, 0, 1, (uint64_t)n * 64});
+        pre = wpre;
+        post = wpost;
+    }
     BatchOp rows{};
     rows.type = kOpRows;
     rows.field = field;
@@ -497,7 +657,9 @@ void plan_batch(Planner &P, int op, const lch_codeword *cws, uint32_t count)
         } else if (!is_pow2(w.k) || w.k == 1) { // shortened code: parity rows as erasures
             mask_buf.assign(w.n, 0);
             std::fill(mask_buf.begin() + w.k, mask_buf.end(), 1);
-            plan_decode(P, c, w.n, w.field, sh, S, mask_buf.data());
+            const auto it = P.ctx->shortened.find(std::make_tuple(w.field, w.n, w.k));
+            plan_decode(P, c, w.n, w.field, sh, S, mask_buf.data(),
+                        it == P.ctx->shortened.end() ? nullptr : it->second);
         } else { // Algorithm 1
             uint8_t *mbar = P.reserve((size_t)w.k * S);
             const uint32_t st = P.add_transform(0, c, w.field, w.k, 0, 1, sh, mbar, S);
@@ -588,13 +750,19 @@ int batch_create(lch_ctx *ctx, int op, const lch_codeword *cws, uint32_t count, 
     if ((rc = validate_batch(op, cws, count))) return rc;
     DeviceScope ds(ctx->device);
     if (!ds.ok) return fail(LCH_ECUDA, "cannot select device %d", ctx->device);
-    // tables and FWHT(log) for every (field, lg n): built once per context
+    // tables and FWHT(log) for every (field, lg n), and the shortened-code
+    // locators of encodes with k not a power of two: built once per context
     for (uint32_t c = 0; c < count; c++) {
-        const uint32_t lgn = lg2(cws[c].n);
-        if ((rc = ensure_tables(ctx, cws[c].field, s))) return rc;
-        if (!ctx->fl[cws[c].field == LCH_GF16][lgn]) {
+        const lch_codeword &w = cws[c];
+        const uint32_t lgn = lg2(w.n);
+        if ((rc = ensure_tables(ctx, w.field, s))) return rc;
+        if (!ctx->fl[w.field == LCH_GF16][lgn]) {
             if ((rc = ensure_scratch(ctx, sizeof(uint32_t) << kBatchMaxLgn))) return rc;
-            if ((rc = ensure_fl(ctx, cws[c].field, lgn, reinterpret_cast<uint32_t *>(ctx->scratch), s))) return rc;
+            if ((rc = ensure_fl(ctx, w.field, lgn, reinterpret_cast<uint32_t *>(ctx->scratch), s))) return rc;
+        }
+        if (op == LCH_BATCH_ENCODE && w.k != w.n && (!is_pow2(w.k) || w.k == 1)) {
+            const uint16_t *loc = nullptr;
+            if ((rc = ensure_shortened(ctx, w.field, w.n, w.k, s, &loc))) return rc;
         }
     }
     Planner sizing{ctx};
@@ -715,6 +883,7 @@ LCH_API void lch_ctx_destroy(lch_ctx *ctx)
         }
         for (auto &row : ctx->fl)
             for (auto *p : row) cudaFree(p);
+        for (auto &kv : ctx->shortened) cudaFree(kv.second);
         cudaFree(ctx->scratch);
         for (auto &r : ctx->prof) {
             cudaEventDestroy(r.a);
@@ -933,6 +1102,78 @@ LCH_API int lch_profile_read(lch_ctx *ctx, int kind, uint64_t *launches, double 
     *total_ms = ms;
     *bytes = by;
     *mults = mu;
+    return LCH_OK;
+}
+
+LCH_API int lch_autotune(lch_ctx *ctx, int field, uint32_t h, size_t shard_bytes, void *stream, lch_tuning *best)
+{
+    int rc;
+    if ((rc = check_field(field)) || (rc = check_len("h", h, field))) return rc;
+    if (h < 2) return fail(LCH_EINVAL, "h must be at least 2 to tune, got %u", h);
+    if (shard_bytes == 0 || (shard_bytes & 15u))
+        return fail(LCH_EINVAL, "shard_bytes must be a nonzero multiple of 16, got %zu", shard_bytes);
+    if (shard_bytes > SIZE_MAX / h) return fail(LCH_EINVAL, "h * shard_bytes overflows");
+    if (!ctx || !best) return fail(LCH_EINVAL, "NULL argument");
+    DeviceScope ds(ctx->device);
+    if (!ds.ok) return fail(LCH_ECUDA, "cannot select device %d", ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ensure_tables(ctx, field, s))) return rc;
+    if ((rc = ensure_scratch(ctx, (size_t)h * shard_bytes))) return rc;
+    uint8_t *buf = ctx->scratch;
+    CU(launch_fill(buf, (size_t)h * shard_bytes, s), "filling the tuning buffer");
+    EventPair ev;
+    if (!ev.ok) return fail(LCH_ECUDA, "cudaEventCreate failed");
+    const bool prof = ctx->prof_on;
+    ctx->prof_on = false; // tuning launches stay out of the profile
+    const uint32_t lgh = lg2(h);
+    uint32_t splits[4];
+    const int ns = tune_splits(lgh, splits);
+    lch_tuning out{};
+    out.ms = -1.f;
+    rc = LCH_OK;
+    for (int i = 0; i < ns && rc == LCH_OK; i++) {
+        const uint32_t a = splits[i], b = lgh - a;
+        uint32_t lg_lo = 0, lg_hi = 0;
+        float ms_lo = 0, ms_hi = 0;
+        rc = tune_pass(ctx, field, h, buf, shard_bytes, 0, a, ev, s, &lg_lo, &ms_lo);
+        if (rc == LCH_OK && b) rc = tune_pass(ctx, field, h, buf, shard_bytes, a, b, ev, s, &lg_hi, &ms_hi);
+        if (rc == LCH_OK && (out.ms < 0 || ms_lo + ms_hi < out.ms)) {
+            out.split = a;
+            out.lg_tile_low = lg_lo;
+            out.lg_tile_high = b ? lg_hi : 0;
+            out.ms = ms_lo + ms_hi;
+        }
+    }
+    ctx->prof_on = prof;
+    if (rc) return rc;
+    ctx->tuned[std::make_tuple(field, lgh, shard_bytes)] = lch_ctx::Plan{out.split, {out.lg_tile_low, out.lg_tile_high}};
+    *best = out;
+    return LCH_OK;
+}
+
+LCH_API int lch_tune_set(lch_ctx *ctx, int field, uint32_t h, size_t shard_bytes, const lch_tuning *plan)
+{
+    int rc;
+    if ((rc = check_field(field)) || (rc = check_len("h", h, field))) return rc;
+    if (h < 2) return fail(LCH_EINVAL, "h must be at least 2 to tune, got %u", h);
+    if (shard_bytes == 0 || (shard_bytes & 15u))
+        return fail(LCH_EINVAL, "shard_bytes must be a nonzero multiple of 16, got %zu", shard_bytes);
+    if (!ctx) return fail(LCH_EINVAL, "ctx is NULL");
+    const uint32_t lgh = lg2(h);
+    const auto key = std::make_tuple(field, lgh, shard_bytes);
+    if (!plan) {
+        ctx->tuned.erase(key);
+        return LCH_OK;
+    }
+    const uint32_t a = plan->split, b = lgh - a;
+    if (a < 1 || a > lgh || a > 8 || b > 8)
+        return fail(LCH_EINVAL, "split %u invalid for lg h = %u (each pass 1..8 levels)", a, lgh);
+    if (plan->lg_tile_low < 4 || plan->lg_tile_low > max_lg_cw(field, a, shard_bytes))
+        return fail(LCH_EINVAL, "lg_tile_low %u outside 4..%u", plan->lg_tile_low, max_lg_cw(field, a, shard_bytes));
+    if (b == 0 && plan->lg_tile_high != 0) return fail(LCH_EINVAL, "lg_tile_high must be 0 for one pass");
+    if (b && (plan->lg_tile_high < 4 || plan->lg_tile_high > max_lg_cw(field, b, shard_bytes)))
+        return fail(LCH_EINVAL, "lg_tile_high %u outside 4..%u", plan->lg_tile_high, max_lg_cw(field, b, shard_bytes));
+    ctx->tuned[key] = lch_ctx::Plan{a, {plan->lg_tile_low, plan->lg_tile_high}};
     return LCH_OK;
 }
 

@@ -157,6 +157,7 @@ struct PassArgs {
     uint32_t l;       // shift
     int inverse;      // 1: (Psi)^-1 order, 0: Psi order
     const uint8_t *rec;
+    uint32_t lg_cw = 0; // log2 column-tile bytes (0: the default for nlev and S)
 };
 cudaError_t launch_pass(int r, const PassArgs &a, cudaStream_t s, uint64_t *launches);
 
@@ -287,5 +288,11 @@ cudaError_t launch_batch(const BatchOp *ops, const BatchTask *tasks, uint32_t nt
                          uint32_t *done, uint32_t ctas, cudaStream_t s, uint64_t *launches);
 // Shared helpers of the planners.
 uint32_t plan_lg_cw(uint32_t nrows, size_t S);
+// Largest log2 column-tile width a pass of 2^nlev rows can use (shared memory).
+uint32_t max_lg_cw(int r, uint32_t nlev, size_t S);
+// ... inside the batch kernel (whose shared memory is fixed).
+uint32_t batch_max_lg_cw(int r, uint32_t nlev);
+// Fill `bytes` bytes with a fixed pseudo-random pattern (autotuning inputs).
+cudaError_t launch_fill(uint8_t *p, size_t bytes, cudaStream_t s);
 
 } // namespace lch

@@ -35,6 +35,17 @@ class Codeword(ctypes.Structure):
                 ("erasure_mask", ctypes.c_void_p)]
 
 
+class Tuning(ctypes.Structure):
+    """struct lch_tuning of include/lch.h."""
+
+    _fields_ = [("split", ctypes.c_uint32), ("lg_tile_low", ctypes.c_uint32), ("lg_tile_high", ctypes.c_uint32),
+                ("ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {"split": int(self.split), "lg_tile_low": int(self.lg_tile_low),
+                "lg_tile_high": int(self.lg_tile_high), "ms": float(self.ms)}
+
+
 class LchError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{message} (status {status})")
@@ -79,6 +90,8 @@ def load() -> ctypes.CDLL:
         "lch_profile_enable": (i, [vp, i]),
         "lch_profile_read": (i, [vp, i, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+        "lch_autotune": (i, [vp, i, u32, sz, vp, ctypes.POINTER(Tuning)]),
+        "lch_tune_set": (i, [vp, i, u32, sz, ctypes.POINTER(Tuning)]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -232,6 +245,22 @@ class Context:
         out = ctypes.c_size_t()
         _check(load().lch_batch_bytes(self._h, op, arr, len(codewords), ctypes.byref(out)))
         return int(out.value)
+
+    def autotune(self, field: int, h: int, shard_bytes: int, stream=None) -> dict:
+        """lch_autotune: time candidate pass plans for (field, h, shard_bytes),
+        keep the fastest on this context and return it."""
+        t = Tuning()
+        _check(load().lch_autotune(self._h, field, h, shard_bytes, _stream_handle(stream), ctypes.byref(t)))
+        return t.as_dict()
+
+    def tune_set(self, field: int, h: int, shard_bytes: int, plan: dict | None):
+        """lch_tune_set: install a plan (a dict as autotune returns), or None
+        to go back to the default plan."""
+        if plan is None:
+            _check(load().lch_tune_set(self._h, field, h, shard_bytes, None))
+            return
+        t = Tuning(int(plan["split"]), int(plan["lg_tile_low"]), int(plan["lg_tile_high"]), float(plan.get("ms", 0.0)))
+        _check(load().lch_tune_set(self._h, field, h, shard_bytes, ctypes.byref(t)))
 
     # Sec. III: Psi_h^l and its inverse, in place on h rows.
     def fft(self, field: int, l: int, buf, stream=None):

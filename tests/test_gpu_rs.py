@@ -137,3 +137,26 @@ def test_large_gf16_workload(ctx):
                  WL.burst_mask(w.n, w.erasures, 0),
                  WL.burst_mask(w.n, w.erasures, WL.random_burst_start(w.n, w.erasures, w.seed))):
         assert np.array_equal(gpu_decode(ctx, w.field, w.n, w.k, cw, mask), cw)
+
+
+def test_shortened_encode_reuses_cached_locator():
+    """k not a power of two: the locator of E = {k..n-1} is computed once per
+    (field, n, k) and reused by later calls and by batches; every use gives the
+    oracle's parity."""
+    ctx2 = lch.Context(0)
+    try:
+        for r, n, k, S in [(16, 1024, 768, 96), (8, 128, 96, 48)]:
+            for rep in range(2):
+                host = message(n, k, S, seed=7000 + rep + n)
+                got = gpu_encode(ctx2, r, n, k, host)
+                cols = elem_cols(S, r, 8, seed=rep)
+                assert np.array_equal(elems(got, r)[:, cols], O.rs_encode(r, n, k, elems(host, r, cols)))
+            hosts = [message(n, k, S, seed=7100 + i) for i in range(2)]
+            devs = [to_dev(h) for h in hosts]
+            b = ctx2.batch(lch.BATCH_ENCODE, [(n, k, r, d, None) for d in devs])
+            b.run()
+            b.status()
+            for h, d in zip(hosts, devs):
+                assert np.array_equal(d.cpu().numpy(), gpu_encode(ctx2, r, n, k, h))
+    finally:
+        ctx2.close()
