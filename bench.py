@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--batch-count", type=int, default=1024)
     p.add_argument("--batch-reps", type=int, default=5)
     p.add_argument("--no-tune", action="store_true", help="keep the default pass plans (no lch_autotune)")
+    p.add_argument("--tune-cache", default=None, help="JSON cache of tuned pass plans (read, and written if new)")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--serve-requests", type=int, default=256)
     return p.parse_args()
@@ -203,7 +204,7 @@ def run_ours(args):
         # encoder, n-point for the decoder), tuned before any timing
         from paper_1404_3458_gb300 import tuning
 
-        plans = tuning.tune(ctx, sorted({(r, k, S), (r, n, S)}))
+        plans = tuning.tune(ctx, sorted({(r, k, S), (r, n, S)}), path=args.tune_cache)
 
     host = np.zeros((n, S), dtype=np.uint8)
     host[:k] = WL.shards(k, S, w.seed + rank)

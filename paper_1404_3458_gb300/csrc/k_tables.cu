@@ -69,16 +69,6 @@ __global__ void k_records(const uint16_t *__restrict__ vals, uint32_t count, uin
 }
 
 template <int R>
-__global__ void k_nibrecs(const uint16_t *__restrict__ vals, uint32_t count, uint8_t *__restrict__ out)
-{
-    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    constexpr uint32_t per = NibRec<R>::subs * 16;
-    if (g >= (uint64_t)count * per) return;
-    const uint32_t f = (uint32_t)(g / per), idx = (uint32_t)(g % per);
-    rec_store<R>(out + (uint64_t)f * NibRec<R>::bytes, idx, nib_entry<R>(vals[f], idx));
-}
-
-template <int R>
 __global__ void k_bconsts(const Consts *__restrict__ c, uint16_t *__restrict__ B, uint16_t *__restrict__ Binv)
 {
     uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -129,8 +119,8 @@ cudaError_t build_impl(FieldTables &t, cudaStream_t s, uint64_t *launches)
     TRY(cudaMalloc(&t.Binv, sizeof(uint16_t) * q));
     TRY(cudaMalloc(&t.expt, sizeof(uint16_t) * q));
     TRY(cudaMalloc(&t.logt, sizeof(uint16_t) * q));
-    TRY(cudaMalloc(&t.bnib, (size_t)NibRec<R>::bytes * q));
-    TRY(cudaMalloc(&t.binvnib, (size_t)NibRec<R>::bytes * q));
+    TRY(cudaMalloc(&t.brec, (size_t)FT<R>::rec_bytes * q));
+    TRY(cudaMalloc(&t.binvrec, (size_t)FT<R>::rec_bytes * q));
     k_consts<R><<<1, 32, 0, s>>>(dc);
     k_factors<R><<<(nf + 255) / 256, 256, 0, s>>>(dc, t.fval);
     {
@@ -140,9 +130,9 @@ cudaError_t build_impl(FieldTables &t, cudaStream_t s, uint64_t *launches)
     k_bconsts<R><<<(q + 255) / 256, 256, 0, s>>>(dc, t.B, t.Binv);
     k_explog<R><<<(q + 255) / 256, 256, 0, s>>>(t.expt, t.logt);
     {
-        const uint64_t total = (uint64_t)q * NibRec<R>::subs * 16;
-        k_nibrecs<R><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(t.B, q, t.bnib);
-        k_nibrecs<R><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(t.Binv, q, t.binvnib);
+        const uint64_t total = (uint64_t)q * FT<R>::rec_entries;
+        k_records<R><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(t.B, q, t.brec);
+        k_records<R><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(t.Binv, q, t.binvrec);
     }
     *launches += 7;
     TRY(cudaGetLastError());

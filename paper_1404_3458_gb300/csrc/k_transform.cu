@@ -26,6 +26,7 @@ constexpr int kPassThreads = 512;
 constexpr uint32_t kTileBytes = 32768; // data bytes per tile
 constexpr int kTargetCtas = 152 * 8;
 constexpr int kSms = 152;
+constexpr size_t kPassSmem = 220 * 1024; // dynamic shared memory of the pass kernels
 
 
 // First record of local level s among the 2^nlev - 1 records of a tile.
@@ -366,53 +367,39 @@ __global__ void __launch_bounds__(kThreads) k_superset(SupersetArgs a, uint32_t 
 
 // ---------------------------------------------------------------- derivative
 // Fused formal derivative over one bit group (Sec. IV.B): with u = B (.) x,
-//   MODE 0: dst = S(u)                   (first of two bit groups)
-//   MODE 1: dst = B^-1 (.) (S(u) ^ xin)  (second group; xin = the first's S)
+//   MODE 0: uout = u, dst = S(u)         (first of two bit groups)
+//   MODE 1: dst = B^-1 (.) (S(u) ^ xin)  (second group; src holds u, xin the
+//                                         first group's S)
 //   MODE 2: dst = B^-1 (.) S(u)          (all bits in one tile)
 // where S(u)_j = XOR over the group's bits l with bit l of j clear of
-// u_{j + 2^l} (eq. XDhx3).  The per-row constants B_j, B_j^-1 use nibble
-// records; a CTA keeps its row group's records in shared memory while it
-// walks its column tiles (cp.async double buffered).
+// u_{j + 2^l} (eq. XDhx3).  B_j and B_j^-1 are per-row constants: the
+// split-table records of the tile's rows (the layout of the butterfly
+// factors, one record per tile row) stay in shared memory while the CTA walks
+// its column tiles (cp.async double buffered).  The first register round
+// multiplies by B as it loads, the last by B^-1 as it stores; a two-group
+// derivative thus multiplies twice per element, and each pass holds one set
+// of 2^nlev records.
 
-template <int R> struct NibRef;
-template <> struct NibRef<16> {
-    uint32_t b0, b1, b2, b3;
-};
-template <> struct NibRef<8> {
-    uint32_t b0, b1;
-};
-// Sub-table k of record q lives at region + (k * nrec + q) * sub_bytes.
-template <int R> __device__ __forceinline__ NibRef<R> nib_ref(uint32_t region, uint32_t q, uint32_t nrec);
-template <> __device__ __forceinline__ NibRef<16> nib_ref<16>(uint32_t region, uint32_t q, uint32_t nrec)
+// Shared-memory offset of chunk c (16 bytes) of record q among nrec records
+// in the region layout of TabRef.
+template <int R> __device__ __forceinline__ uint32_t rec_dst(uint32_t nrec, uint32_t q, uint32_t c)
 {
-    const uint32_t b = region + (q << 5);
-    return {b, b + (nrec << 5), b + (nrec << 6), b + nrec * 96u};
-}
-template <> __device__ __forceinline__ NibRef<8> nib_ref<8>(uint32_t region, uint32_t q, uint32_t nrec)
-{
-    const uint32_t b = region + (q << 4);
-    return {b, b + (nrec << 4)};
+    if constexpr (R == 16)
+        return c < 8 ? (q << 7) + (c << 4) : (c < 16 ? ((nrec + q) << 7) + ((c - 8) << 4) : (nrec << 8) + (q << 5) + ((c - 16) << 4));
+    else
+        return (q << 8) + (c << 4);
 }
 
-template <int R> __device__ __forceinline__ uint32_t mul_nib(uint32_t w, const NibRef<R> &t);
-template <> __device__ __forceinline__ uint32_t mul_nib<16>(uint32_t w, const NibRef<16> &t)
-{
-    const uint32_t lo = lds_u16<0>(((w << 1) & 0x1Eu) | t.b0) ^ lds_u16<0>(((w >> 3) & 0x1Eu) | t.b1) ^
-                        lds_u16<0>(((w >> 7) & 0x1Eu) | t.b2) ^ lds_u16<0>(((w >> 11) & 0x1Eu) | t.b3);
-    const uint32_t hi = lds_u16<0>(((w >> 15) & 0x1Eu) | t.b0) ^ lds_u16<0>(((w >> 19) & 0x1Eu) | t.b1) ^
-                        lds_u16<0>(((w >> 23) & 0x1Eu) | t.b2) ^ lds_u16<0>(((w >> 27) & 0x1Eu) | t.b3);
-    return lo | (hi << 16);
-}
-template <> __device__ __forceinline__ uint32_t mul_nib<8>(uint32_t w, const NibRef<8> &t)
-{
-    uint32_t r = 0;
-#pragma unroll
-    for (int b = 0; b < 4; b++) {
-        const uint32_t v = lds_u8<0>(((w >> (8 * b)) & 0xFu) | t.b0) ^ lds_u8<0>(((w >> (8 * b + 4)) & 0xFu) | t.b1);
-        r |= v << (8 * b);
+// x[U] *= the constant of record (base | U << S0), U < N; t refers to base.
+template <int R, int N, int S0, int U = 0> struct RowMul {
+    static __device__ __forceinline__ void run(uint32_t *x, const TabRef<R> &t)
+    {
+        if constexpr (U < N) {
+            x[U] = MulK<R, ((uint32_t)U << S0)>::f(x[U], t);
+            RowMul<R, N, S0, U + 1>::run(x, t);
+        }
     }
-    return r;
-}
+};
 
 // Neighbour sums inside one register group of 2^Q rows (bits s0 .. s0+Q-1 of
 // the tile-local row index): acc[u] ^= x[u | 2^b] for every b < Q with bit b
@@ -431,70 +418,152 @@ template <int Q, int U, int B> struct NbrSum {
     }
 };
 
-// Round over bits [s0, s0+Q) of a tile.  FIRST: acc = S_round(u) (^ the
-// acc tile when it already holds xin) -> acc tile.  LAST: out = B^-1? (acc
-// tile ^ S_round(u)) -> global.  A round can be both (single-round tiles).
-template <int R, int Q, bool FIRST, bool LAST, bool INV>
-__device__ __forceinline__ void deriv_round(const DerivArgs &a, uint32_t su, uint32_t sacc, bool acc_has_data,
-                                            uint32_t s_binv, uint32_t nrows, uint32_t lg_w, uint32_t s0,
-                                            uint32_t hibase, uint32_t lo, size_t col, uint32_t width)
+// One register round over tile bits [S0, S0+Q).  FIRST: when MULB, x is
+// multiplied by B as it is loaded (written back as u when another round
+// follows, and to uout when UOUT); the sums start at zero, or at the
+// accumulator tile (xin) when ACC_IN.  LAST: the sums, times B^-1 when INV, go
+// to global memory; otherwise to the accumulator tile.
+template <int R, int Q, int S0, bool FIRST, bool LAST, bool ACC_IN, bool INV, bool MULB, bool UOUT>
+__device__ __forceinline__ void deriv_round(const DerivArgs &a, uint32_t su, uint32_t sacc, uint32_t s_b,
+                                            uint32_t s_binv, uint32_t nrows, uint32_t lg_w, uint32_t hibase,
+                                            uint32_t lo, size_t col, uint32_t width)
 {
     const uint32_t W = 1u << lg_w;
     const uint32_t items = (nrows >> Q) << lg_w;
-    const uint32_t stride = 4u << (s0 + lg_w);
+    const uint32_t stride = 4u << (S0 + lg_w);
     for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
         const uint32_t g = it >> lg_w, w = it & (W - 1u);
-        const uint32_t base = ((g >> s0) << (s0 + Q)) | (g & ((1u << s0) - 1u));
+        const uint32_t base = ((g >> S0) << (S0 + Q)) | (g & ((1u << S0) - 1u));
         const uint32_t off = ((base << lg_w) + w) << 2;
         uint32_t x[1 << Q], acc[1 << Q];
 #pragma unroll
         for (int u = 0; u < (1 << Q); u++) x[u] = lds_u32(su + off + u * stride);
+        if constexpr (FIRST && MULB) {
+            const TabRef<R> t = tab_ref<R>(s_b, base, nrows);
+            RowMul<R, (1 << Q), S0>::run(x, t);
+            if constexpr (!LAST) {
 #pragma unroll
-        for (int u = 0; u < (1 << Q); u++) acc[u] = (!FIRST || acc_has_data) ? lds_u32(sacc + off + u * stride) : 0u;
+                for (int u = 0; u < (1 << Q); u++) sts_u32(su + off + u * stride, x[u]);
+            }
+            if constexpr (UOUT) {
+                if (w * 4 < width) {
+                    const size_t row0 = hibase | ((size_t)base << a.L0) | lo;
+                    uint8_t *p = a.uout + row0 * a.S + col + w * 4;
+                    const size_t rstep = a.S << (S0 + a.L0);
+#pragma unroll
+                    for (int u = 0; u < (1 << Q); u++) *reinterpret_cast<uint32_t *>(p + u * rstep) = x[u];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < (1 << Q); u++) acc[u] = (!FIRST || ACC_IN) ? lds_u32(sacc + off + u * stride) : 0u;
         NbrSum<Q, 0, 0>::run(x, acc);
         if constexpr (!LAST) {
 #pragma unroll
             for (int u = 0; u < (1 << Q); u++) sts_u32(sacc + off + u * stride, acc[u]);
         } else {
+            if constexpr (INV) {
+                const TabRef<R> t = tab_ref<R>(s_binv, base, nrows);
+                RowMul<R, (1 << Q), S0>::run(acc, t);
+            }
             if (w * 4 < width) {
                 const size_t row0 = hibase | ((size_t)base << a.L0) | lo;
                 uint8_t *p = a.dst + row0 * a.S + col + w * 4;
-                const size_t rstep = a.S << (s0 + a.L0);
+                const size_t rstep = a.S << (S0 + a.L0);
 #pragma unroll
-                for (int u = 0; u < (1 << Q); u++) {
-                    uint32_t v = acc[u];
-                    if constexpr (INV) v = mul_nib<R>(v, nib_ref<R>(s_binv, base | ((uint32_t)u << s0), nrows));
-                    *reinterpret_cast<uint32_t *>(p + u * rstep) = v;
-                }
+                for (int u = 0; u < (1 << Q); u++) *reinterpret_cast<uint32_t *>(p + u * rstep) = acc[u];
             }
         }
     }
 }
 
-template <int R, bool FIRST, bool LAST, bool INV>
-__device__ __forceinline__ void deriv_round_q(uint32_t q, const DerivArgs &a, uint32_t su, uint32_t sacc,
-                                              bool acc_has_data, uint32_t s_binv, uint32_t nrows, uint32_t lg_w,
-                                              uint32_t s0, uint32_t hibase, uint32_t lo, size_t col, uint32_t width)
+// The rounds of one tile: 4-bit rounds when the tile has at least 16 column
+// words per thread (every thread busy in a 4-bit round), else rounds of at
+// most 3 bits.
+template <int R, int MODE>
+__device__ __forceinline__ void deriv_tile(const DerivArgs &a, uint32_t su, uint32_t sacc, uint32_t s_b,
+                                           uint32_t s_binv, uint32_t lg_w, uint32_t hibase, uint32_t lo, size_t col,
+                                           uint32_t width)
 {
-    switch (q) {
-    case 1: deriv_round<R, 1, FIRST, LAST, INV>(a, su, sacc, acc_has_data, s_binv, nrows, lg_w, s0, hibase, lo, col, width); break;
-    case 2: deriv_round<R, 2, FIRST, LAST, INV>(a, su, sacc, acc_has_data, s_binv, nrows, lg_w, s0, hibase, lo, col, width); break;
-    case 3: deriv_round<R, 3, FIRST, LAST, INV>(a, su, sacc, acc_has_data, s_binv, nrows, lg_w, s0, hibase, lo, col, width); break;
-    default: deriv_round<R, 4, FIRST, LAST, INV>(a, su, sacc, acc_has_data, s_binv, nrows, lg_w, s0, hibase, lo, col, width); break;
+    constexpr bool kX = MODE == 1, kInv = MODE != 0, kMulB = MODE != 1, kUout = MODE == 0;
+    const uint32_t nrows = 1u << a.nlev;
+    const bool wide = (nrows << lg_w) >= 16u * blockDim.x;
+#define LCH_DR(Q, S0, F, L, X, I)                                                                 \
+    deriv_round<R, Q, S0, F, L, X, I, kMulB, kUout>(a, su, sacc, s_b, s_binv, nrows, lg_w, hibase, lo, col, width)
+#define LCH_SYNC __syncthreads()
+    switch (a.nlev) {
+    case 1: LCH_DR(1, 0, true, true, kX, kInv); break;
+    case 2: LCH_DR(2, 0, true, true, kX, kInv); break;
+    case 3: LCH_DR(3, 0, true, true, kX, kInv); break;
+    case 4:
+        if (wide) {
+            LCH_DR(4, 0, true, true, kX, kInv);
+        } else {
+            LCH_DR(2, 0, true, false, kX, false);
+            LCH_SYNC;
+            LCH_DR(2, 2, false, true, true, kInv);
+        }
+        break;
+    case 5:
+        LCH_DR(3, 0, true, false, kX, false);
+        LCH_SYNC;
+        LCH_DR(2, 3, false, true, true, kInv);
+        break;
+    case 6:
+        LCH_DR(3, 0, true, false, kX, false);
+        LCH_SYNC;
+        LCH_DR(3, 3, false, true, true, kInv);
+        break;
+    case 7:
+        if (wide) {
+            LCH_DR(4, 0, true, false, kX, false);
+            LCH_SYNC;
+            LCH_DR(3, 4, false, true, true, kInv);
+        } else {
+            LCH_DR(3, 0, true, false, kX, false);
+            LCH_SYNC;
+            LCH_DR(2, 3, false, false, true, false);
+            LCH_SYNC;
+            LCH_DR(2, 5, false, true, true, kInv);
+        }
+        break;
+    default:
+        if (wide) {
+            LCH_DR(4, 0, true, false, kX, false);
+            LCH_SYNC;
+            LCH_DR(4, 4, false, true, true, kInv);
+        } else {
+            LCH_DR(3, 0, true, false, kX, false);
+            LCH_SYNC;
+            LCH_DR(3, 3, false, false, true, false);
+            LCH_SYNC;
+            LCH_DR(2, 6, false, true, true, kInv);
+        }
+        break;
     }
+#undef LCH_SYNC
+#undef LCH_DR
+}
+
+// Records a derivative pass keeps: B (mode 0), B^-1 (mode 1) or both (mode 2).
+template <int R>
+__host__ __device__ __forceinline__ uint32_t deriv_rec_bytes(uint32_t nrows, int mode)
+{
+    return (mode == 2 ? 2u : 1u) * tab_bytes<R>(nrows);
 }
 
 template <int R, int MODE>
 __device__ __forceinline__ void deriv_body(const DerivArgs &a, uint32_t lg_cw, uint32_t g, uint32_t y0, uint32_t ystep,
                                            uint8_t *sm)
 {
-    constexpr bool kX = MODE == 1, kInv = MODE != 0;
+    constexpr bool kX = MODE == 1, kMulB = MODE != 1, kInv = MODE != 0;
+    constexpr uint32_t kSets = (kMulB ? 1 : 0) + (kInv ? 1 : 0);
     const uint32_t nlev = a.nlev, nrows = 1u << nlev;
     const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
-    const uint32_t rec_bytes = nrows * NibRec<R>::bytes;
-    const uint32_t s_brec = (uint32_t)__cvta_generic_to_shared(sm);
-    const uint32_t s_binv = s_brec + rec_bytes;
-    uint8_t *stage0 = sm + (kInv ? 2 : 1) * rec_bytes;
+    const uint32_t rec_bytes = tab_bytes<R>(nrows);
+    const uint32_t s_b = (uint32_t)__cvta_generic_to_shared(sm);
+    const uint32_t s_binv = s_b + (kMulB ? rec_bytes : 0);
+    uint8_t *stage0 = sm + deriv_rec_bytes<R>(nrows, MODE);
     const uint32_t tile_bytes = nrows << lg_cw;
     const uint32_t stage_bytes = 2 * tile_bytes; // u tile + accumulator tile
     const uint32_t lo = g & ((1u << a.L0) - 1u);
@@ -503,15 +572,15 @@ __device__ __forceinline__ void deriv_body(const DerivArgs &a, uint32_t lg_cw, u
     const size_t col0 = (size_t)y0 << lg_cw;
     const uint32_t ntiles = col0 < a.S ? (uint32_t)((a.S - col0 + col_step - 1) / col_step) : 0;
 
-    // Records of the tile rows, laid out by sub-table (see nib_ref).
-    constexpr uint32_t cpr = NibRec<R>::bytes / 16, cps = NibRec<R>::sub_bytes / 16;
-    for (uint32_t v = threadIdx.x; v < nrows * cpr * (kInv ? 2 : 1); v += blockDim.x) {
-        const uint32_t which = v / (nrows * cpr), vv = v - which * nrows * cpr;
+    // Records of B and/or B^-1 for the tile rows.
+    constexpr uint32_t cpr = FT<R>::rec_bytes / 16;
+    for (uint32_t v = threadIdx.x; v < nrows * cpr * kSets; v += blockDim.x) {
+        const uint32_t set = v / (nrows * cpr), vv = v - set * nrows * cpr;
         const uint32_t q = vv / cpr, c = vv - q * cpr;
-        const uint32_t k = c / cps, part = c - k * cps;
         const size_t row = hibase | ((size_t)q << a.L0) | lo;
-        const uint8_t *src = (which ? a.binvnib : a.bnib) + row * NibRec<R>::bytes + c * 16;
-        cp_async16(sm + which * rec_bytes + (k * nrows + q) * NibRec<R>::sub_bytes + part * 16, src);
+        const bool inv = !kMulB || set == 1;
+        const uint8_t *src = (inv ? a.binvrec : a.brec) + row * FT<R>::rec_bytes + c * 16;
+        cp_async16(sm + set * rec_bytes + rec_dst<R>(nrows, q, c), src);
     }
 
     auto issue = [&](uint32_t t, uint8_t *dstbuf) {
@@ -532,7 +601,6 @@ __device__ __forceinline__ void deriv_body(const DerivArgs &a, uint32_t lg_cw, u
     if (ntiles > 1) issue(1, stage0 + stage_bytes);
     cp_async_commit();
 
-    const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, qb = nlev - qa;
     for (uint32_t t = 0; t < ntiles; t++) {
         uint8_t *stage = stage0 + (t & 1u) * stage_bytes;
         const uint32_t su = (uint32_t)__cvta_generic_to_shared(stage), sacc = su + tile_bytes;
@@ -541,34 +609,7 @@ __device__ __forceinline__ void deriv_body(const DerivArgs &a, uint32_t lg_cw, u
         const uint32_t width = rem < cw ? (uint32_t)rem : cw;
         cp_async_wait1();
         __syncthreads();
-        // u = B (.) x, in place; 8 independent words per thread for ILP.
-        const uint32_t items = nrows << lg_w;
-        for (uint32_t it0 = threadIdx.x; it0 < items; it0 += 8 * blockDim.x) {
-            uint32_t x[8];
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const uint32_t it = it0 + j * blockDim.x;
-                x[j] = it < items ? lds_u32(su + (it << 2)) : 0u;
-            }
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const uint32_t it = it0 + j * blockDim.x;
-                if (it < items) x[j] = mul_nib<R>(x[j], nib_ref<R>(s_brec, it >> lg_w, nrows));
-            }
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const uint32_t it = it0 + j * blockDim.x;
-                if (it < items) sts_u32(su + (it << 2), x[j]);
-            }
-        }
-        __syncthreads();
-        if (qb == 0) {
-            deriv_round_q<R, true, true, kInv>(qa, a, su, sacc, kX, s_binv, nrows, lg_w, 0, hibase, lo, col, width);
-        } else {
-            deriv_round_q<R, true, false, kInv>(qa, a, su, sacc, kX, s_binv, nrows, lg_w, 0, hibase, lo, col, width);
-            __syncthreads();
-            deriv_round_q<R, false, true, kInv>(qb, a, su, sacc, true, s_binv, nrows, lg_w, qa, hibase, lo, col, width);
-        }
+        deriv_tile<R, MODE>(a, su, sacc, s_b, s_binv, lg_w, hibase, lo, col, width);
         __syncthreads();
         if (t + 2 < ntiles) issue(t + 2, stage);
         cp_async_commit();
@@ -640,6 +681,18 @@ dim3 pick_grid(uint32_t ngroups, size_t S, uint32_t lg_cw)
     if (y < 1) y = 1;
     if (y > 65535) y = 65535;
     return dim3(ngroups, (unsigned)y, 1);
+}
+
+// Column tile width of a derivative pass: the default, narrowed until the
+// records and two stages of two tiles fit in `budget` bytes.
+template <int R>
+uint32_t deriv_lg_cw(uint32_t nlev, int mode, size_t S, size_t budget)
+{
+    const uint32_t nrows = 1u << nlev;
+    const size_t rec = deriv_rec_bytes<R>(nrows, mode);
+    uint32_t lg = pick_lg_cw(nrows, S);
+    while (lg > 4 && rec + 4 * ((size_t)nrows << lg) > budget) lg--;
+    return lg;
 }
 
 template <int R, int INV>
@@ -731,7 +784,7 @@ __device__ __forceinline__ void run_task(const BatchOp &op, const BatchTask &t, 
         break;
     }
     default: {
-        DerivArgs a{op.src, op.xin, op.dst, op.S, op.h, op.L0, op.nlev, op.tab0, op.tab1};
+        DerivArgs a{op.src, op.aux, op.dst, op.S, op.h, op.L0, op.nlev, op.tab0, op.tab1, op.aux};
         for (uint32_t g = t.g0; g < t.g1; g++) {
             if (op.mode == 0)
                 deriv_body<R, 0>(a, op.lg_cw, g, 0, 1, sm);
@@ -754,9 +807,9 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
 
 constexpr uint32_t kMaxWaitSpins = 1u << 24; // ~1-2 s with the back-off below
 
-// Shared memory of the largest task body: the second derivative pass of
-// GF(2^16) (2 x 256 nibble records + 2 stages of 2 tiles).
-__host__ __device__ constexpr size_t batch_body_smem() { return 2 * 256 * NibRec<16>::bytes + 4 * (size_t)kTileBytes; }
+// Shared memory of a batch task body (the largest: a derivative pass with
+// 2 x 256 GF(2^16) records and 2 stages of 2 tiles; tiles are narrowed to fit).
+__host__ __device__ constexpr size_t batch_body_smem() { return 192 * 1024; }
 
 // The persistent batch kernel: one CTA per SM pulls tasks in queue order.
 __global__ void __launch_bounds__(kPassThreads, 1)
@@ -846,7 +899,7 @@ cudaError_t launch_pointwise(int r, uint8_t *c, const uint8_t *t, size_t bytes, 
 
 cudaError_t configure_transform_kernels()
 {
-    const int big = 220 * 1024;
+    const int big = (int)kPassSmem;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_pass<8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_pass<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
@@ -865,9 +918,15 @@ cudaError_t configure_transform_kernels()
 
 uint32_t plan_lg_cw(uint32_t nrows, size_t S) { return pick_lg_cw(nrows, S); }
 
+uint32_t plan_deriv_lg_cw(int r, uint32_t nlev, int mode, size_t S, bool batch)
+{
+    const size_t budget = batch ? batch_body_smem() : kPassSmem;
+    return r == 16 ? deriv_lg_cw<16>(nlev, mode, S, budget) : deriv_lg_cw<8>(nlev, mode, S, budget);
+}
+
 uint32_t max_lg_cw(int r, uint32_t nlev, size_t S)
 {
-    const size_t budget = 220 * 1024;
+    const size_t budget = kPassSmem;
     const size_t tab = r == 16 ? tab_bytes<16>((1u << nlev) - 1) : tab_bytes<8>((1u << nlev) - 1);
     uint32_t lg = 4;
     while (lg < 12 && tab + (2ull << nlev << (lg + 1)) <= budget && (1ull << (lg + 1)) < 2 * S) lg++;
@@ -933,9 +992,8 @@ template <int R, int MODE>
 cudaError_t deriv_impl(const DerivArgs &a, cudaStream_t s)
 {
     const uint32_t nrows = 1u << a.nlev;
-    const uint32_t lg_cw = pick_lg_cw(nrows, a.S);
-    const size_t rec = (size_t)nrows * NibRec<R>::bytes * (MODE == 0 ? 1 : 2);
-    const size_t smem = rec + 2 * 2 * ((size_t)nrows << lg_cw);
+    const uint32_t lg_cw = deriv_lg_cw<R>(a.nlev, MODE, a.S, kPassSmem);
+    const size_t smem = deriv_rec_bytes<R>(nrows, MODE) + 2 * 2 * ((size_t)nrows << lg_cw);
     const uint32_t ngroups = a.h >> a.nlev;
     const size_t ntiles = (a.S + (1ull << lg_cw) - 1) >> lg_cw;
     size_t y = (ntiles + 7) / 8;

@@ -332,7 +332,8 @@ int tune_pass(lch_ctx *ctx, int field, uint32_t h, uint8_t *buf, size_t S, uint3
 
 // dst = [src]' (coefficient vectors of h rows): u = B (.) src, neighbour sums
 // split by bit group, B^-1 (.) (Sec. IV.B).  dst may equal src.
-int derivative(lch_ctx *ctx, int field, uint32_t h, const uint8_t *src, uint8_t *dst, uint8_t *tmp, size_t S,
+// With two bit groups src is overwritten with B (.) src.
+int derivative(lch_ctx *ctx, int field, uint32_t h, uint8_t *src, uint8_t *dst, uint8_t *tmp, size_t S,
                cudaStream_t s)
 {
     const FieldTables &t = ctx->tab[field == LCH_GF16];
@@ -344,18 +345,20 @@ int derivative(lch_ctx *ctx, int field, uint32_t h, const uint8_t *src, uint8_t 
     uint32_t a, b;
     split_levels(lgh, &a, &b);
     const uint64_t elems = (uint64_t)h * (S / (field / 8));
-    DerivArgs d{src, nullptr, dst, S, h, 0, a, t.bnib, t.binvnib};
+    DerivArgs d{src, nullptr, dst, S, h, 0, a, t.brec, t.binvrec};
     if (b == 0) {
         PROFM(LCH_KIND_DERIV, 2ull * h * S, 2 * elems, launch_deriv(field, 2, d, s, &ctx->launches));
         return LCH_OK;
     }
-    d.dst = tmp; // S_low(u)
-    PROFM(LCH_KIND_DERIV, 2ull * h * S, elems, launch_deriv(field, 0, d, s, &ctx->launches));
+    d.dst = tmp;  // S_low(u)
+    d.uout = src; // u = B (.) x over x
+    PROFM(LCH_KIND_DERIV, 3ull * h * S, elems, launch_deriv(field, 0, d, s, &ctx->launches));
     d.xin = tmp;
     d.dst = dst;
+    d.uout = nullptr;
     d.L0 = a;
     d.nlev = b;
-    PROFM(LCH_KIND_DERIV, 3ull * h * S, 2 * elems, launch_deriv(field, 1, d, s, &ctx->launches));
+    PROFM(LCH_KIND_DERIV, 3ull * h * S, elems, launch_deriv(field, 1, d, s, &ctx->launches));
     return LCH_OK;
 }
 
@@ -609,27 +612,28 @@ void plan_decode(Planner &P, uint32_t cw, uint32_t n, int field, uint8_t *shards
     d.S = S;
     d.h = n;
     d.src = phi;
-    d.tab0 = t.bnib;
-    d.tab1 = t.binvnib;
+    d.tab0 = t.brec;
+    d.tab1 = t.binvrec;
     if (b == 0) {
         d.mode = 2;
         d.dst = phi2;
         d.L0 = 0;
         d.nlev = a;
-        d.lg_cw = plan_lg_cw(1u << a, S);
+        d.lg_cw = plan_deriv_lg_cw(field, a, 2, S, true);
         P.add_tasks(stage++, P.add_op(d), cw, n >> a, ((size_t)1 << a) * S);
     } else {
         d.mode = 0;
         d.dst = phi2;
+        d.aux = phi; // u = B (.) x over x
         d.L0 = 0;
         d.nlev = a;
-        d.lg_cw = plan_lg_cw(1u << a, S);
+        d.lg_cw = plan_deriv_lg_cw(field, a, 0, S, true);
         P.add_tasks(stage++, P.add_op(d), cw, n >> a, ((size_t)1 << a) * S);
         d.mode = 1;
-        d.xin = phi2;
+        d.aux = phi2;
         d.L0 = a;
         d.nlev = b;
-        d.lg_cw = plan_lg_cw(1u << b, S);
+        d.lg_cw = plan_deriv_lg_cw(field, b, 1, S, true);
         P.add_tasks(stage++, P.add_op(d), cw, n >> b, ((size_t)1 << b) * S);
     }
     stage = P.add_transform(stage, cw, field, n, 0, 0, phi2, phi2, S);
@@ -878,8 +882,8 @@ LCH_API void lch_ctx_destroy(lch_ctx *ctx)
             cudaFree(t.Binv);
             cudaFree(t.expt);
             cudaFree(t.logt);
-            cudaFree(t.bnib);
-            cudaFree(t.binvnib);
+            cudaFree(t.brec);
+            cudaFree(t.binvrec);
         }
         for (auto &row : ctx->fl)
             for (auto *p : row) cudaFree(p);

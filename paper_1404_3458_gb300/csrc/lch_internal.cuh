@@ -96,19 +96,6 @@ template <> __device__ __forceinline__ uint32_t mul_word<16>(uint32_t w, const u
     return lo | (hi << 16);
 }
 
-// "Nibble" record of a constant c: r/4 sub-tables of 16 entries, sub-table k
-// holding c * (e << 4k).  Smaller than a split-table record (4 lookups per
-// GF(2^16) element instead of 3), used for per-row constants.
-template <int R> struct NibRec {
-    static constexpr uint32_t subs = R / 4;
-    static constexpr uint32_t sub_bytes = 16 * (R / 8);
-    static constexpr uint32_t bytes = subs * sub_bytes; // 128 (GF(2^16)) or 32 (GF(2^8))
-};
-template <int R> __device__ __forceinline__ uint32_t nib_entry(uint32_t c, uint32_t idx)
-{
-    return gf_mul_slow<R>(c, (idx & 15u) << (4 * (idx >> 4)));
-}
-
 // Offset of level i in the per-level factor arrays: level i holds 2^(r-i)
 // entries, one per value of (x >> i), x in [0, 2^r).
 __host__ __device__ __forceinline__ uint32_t level_off(int r, int i)
@@ -127,8 +114,8 @@ struct FieldTables {
     uint16_t *Binv = nullptr; // B_j^-1
     uint16_t *expt = nullptr; // alpha^i, i < 2^r - 1
     uint16_t *logt = nullptr; // log_alpha(x), x != 0; logt[0] = 0
-    uint8_t *bnib = nullptr;  // nibble record of B_j, j < 2^r (NibRec<r>::bytes each)
-    uint8_t *binvnib = nullptr; // nibble record of B_j^-1
+    uint8_t *brec = nullptr;    // split-table record of B_j, j < 2^r (FT<r>::rec_bytes each)
+    uint8_t *binvrec = nullptr; // split-table record of B_j^-1
     uint32_t wbase[16] = {};  // W_i(w_{2^i}) (host copy, for tests/diagnostics)
 };
 
@@ -174,8 +161,9 @@ struct SupersetArgs {
 };
 cudaError_t launch_superset(const SupersetArgs &a, cudaStream_t s, uint64_t *launches);
 
-// Fused derivative over one bit group: see k_deriv.  mode 0: dst = S(B x);
-// mode 1: dst = B^-1 (S(B x) ^ xin); mode 2: dst = B^-1 S(B x).
+// Fused derivative over one bit group: see k_deriv.  mode 0: u = B x is
+// written to uout (may be src) and dst = S(u); mode 1 (src holds u):
+// dst = B^-1 (S(u) ^ xin); mode 2: dst = B^-1 S(B x).
 struct DerivArgs {
     const uint8_t *src;
     const uint8_t *xin;
@@ -184,8 +172,9 @@ struct DerivArgs {
     uint32_t h;
     uint32_t L0;
     uint32_t nlev;
-    const uint8_t *bnib;
-    const uint8_t *binvnib;
+    const uint8_t *brec;    // split-table records of B_j, j < 2^r
+    const uint8_t *binvrec; // ... of B_j^-1
+    uint8_t *uout = nullptr; // mode 0: destination of u = B (.) x
 };
 cudaError_t launch_deriv(int r, int mode, const DerivArgs &a, cudaStream_t s, uint64_t *launches);
 
@@ -263,12 +252,12 @@ enum BatchOpType : uint32_t { kOpLocator = 0, kOpRows = 1, kOpPass = 2, kOpDeriv
 struct BatchOp {
     uint32_t type, field, mode, lg_cw;
     const uint8_t *src;
-    const uint8_t *xin;
+    uint8_t *aux;          // deriv mode 0: u = B (.) x goes here; mode 1: S of the first group
     uint8_t *dst;
     size_t S;
     uint32_t h, L0, nlev, l;
-    const uint8_t *tab0;   // pass: factor records; deriv: B nibble records; locator: FWHT(L)
-    const uint8_t *tab1;   // deriv: B^-1 nibble records; locator: exp table
+    const uint8_t *tab0;   // pass: factor records; deriv: B_j records; locator: FWHT(L)
+    const uint8_t *tab1;   // deriv: B_j^-1 records; locator: exp table
     const uint16_t *coef;  // rows: per-row constants; locator: log table
     const uint32_t *mask;  // locator: erasure bitmap (n bits)
     uint16_t *pre, *post;  // locator outputs
@@ -288,6 +277,9 @@ cudaError_t launch_batch(const BatchOp *ops, const BatchTask *tasks, uint32_t nt
                          uint32_t *done, uint32_t ctas, cudaStream_t s, uint64_t *launches);
 // Shared helpers of the planners.
 uint32_t plan_lg_cw(uint32_t nrows, size_t S);
+// Column tile width of a derivative pass of 2^nlev rows in mode `mode`, for
+// the derivative kernel or (batch) the batch kernel.
+uint32_t plan_deriv_lg_cw(int r, uint32_t nlev, int mode, size_t S, bool batch);
 // Largest log2 column-tile width a pass of 2^nlev rows can use (shared memory).
 uint32_t max_lg_cw(int r, uint32_t nlev, size_t S);
 // ... inside the batch kernel (whose shared memory is fixed).
