@@ -112,6 +112,49 @@ template <uint32_t K> struct MulK<8, K> {
     static __device__ __forceinline__ uint32_t f(uint32_t w, const TabRef<8> &t) { return mul8<K * 256>(w, t); }
 };
 
+// Chunk c (16 bytes) of the split-table record of constant k, computed from
+// the products k x^b alone (no tables): entry e of a sub-table whose first
+// power is x^o is the XOR of k x^(o+b) over the set bits b of e.
+__device__ __forceinline__ uint32_t xtime16(uint32_t v)
+{
+    v <<= 1;
+    return (v & 0x10000u) ? v ^ FT<16>::poly : v;
+}
+__device__ __forceinline__ uint32_t xtime8(uint32_t v)
+{
+    v <<= 1;
+    return (v & 0x100u) ? v ^ FT<8>::poly : v;
+}
+template <int R> __device__ __forceinline__ uint4 rec_chunk(uint32_t k, uint32_t c);
+template <> __device__ __forceinline__ uint4 rec_chunk<16>(uint32_t k, uint32_t c)
+{
+    // chunks 0-7: k e (e < 64); 8-15: k (e << 6); 16-17: k (e << 12) (e < 16)
+    const uint32_t o = c < 8 ? 0 : (c < 16 ? 6 : 12), q = c - (c < 8 ? 0 : (c < 16 ? 8 : 16));
+    uint32_t p0 = k;
+    for (uint32_t i = 0; i < o; i++) p0 = xtime16(p0);
+    const uint32_t p1 = xtime16(p0), p2 = xtime16(p1), p3 = xtime16(p2), p4 = xtime16(p3), p5 = xtime16(p4);
+    const uint32_t e0 = ((q & 1u) ? p3 : 0u) ^ ((q & 2u) ? p4 : 0u) ^ ((q & 4u) ? p5 : 0u); // entries 8q .. 8q+7
+    const uint32_t e1 = e0 ^ p0, e2 = e0 ^ p1, e3 = e1 ^ p1;
+    const uint32_t e4 = e0 ^ p2, e5 = e1 ^ p2, e6 = e2 ^ p2, e7 = e3 ^ p2;
+    return make_uint4(e0 | (e1 << 16), e2 | (e3 << 16), e4 | (e5 << 16), e6 | (e7 << 16));
+}
+template <> __device__ __forceinline__ uint4 rec_chunk<8>(uint32_t k, uint32_t c)
+{
+    // entries 16c .. 16c+15 of the 256 products k e
+    uint32_t p[8];
+    p[0] = k;
+#pragma unroll
+    for (int b = 1; b < 8; b++) p[b] = xtime8(p[b - 1]);
+    uint32_t e[16];
+    e[0] = ((c & 1u) ? p[4] : 0u) ^ ((c & 2u) ? p[5] : 0u) ^ ((c & 4u) ? p[6] : 0u) ^ ((c & 8u) ? p[7] : 0u);
+#pragma unroll
+    for (int r = 1; r < 16; r++) e[r] = e[r & (r - 1)] ^ p[(r & 1) ? 0 : (r & 2) ? 1 : (r & 4) ? 2 : 3];
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) w[i] = e[4 * i] | (e[4 * i + 1] << 8) | (e[4 * i + 2] << 16) | (e[4 * i + 3] << 24);
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 // Butterflies of local level j (0 <= j < Q) on the 2^Q registers x[], whose
 // row u is tile row base | (u << s0).  The pair (u, u + 2^j) belongs to block
 // (base >> (s0+j+1)) + (u >> (j+1)) of level s0 + j.
@@ -625,31 +668,58 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_deriv(DerivArgs a, uint32_t
     deriv_body<R, MODE>(a, lg_cw, blockIdx.x, blockIdx.y, gridDim.y, sm);
 }
 
+// Per-row scaling dst[row] = coef[row] (.) src[row] for kRowsPerCta rows per
+// CTA.  The rows' split-table records are computed in shared memory
+// (rec_chunk); a row with coef 0 is not read: it is written as zeros, or left
+// alone when skip_zero.
+constexpr uint32_t kRowsPerCta = 8;
+
+template <int R, uint32_t Q = 0> struct RowsScale {
+    static __device__ __forceinline__ void run(uint4 *x, const uint32_t *k, const TabRef<R> &t)
+    {
+        if constexpr (Q < kRowsPerCta) {
+            if (k[Q]) {
+                x[Q].x = MulK<R, Q>::f(x[Q].x, t);
+                x[Q].y = MulK<R, Q>::f(x[Q].y, t);
+                x[Q].z = MulK<R, Q>::f(x[Q].z, t);
+                x[Q].w = MulK<R, Q>::f(x[Q].w, t);
+            }
+            RowsScale<R, Q + 1>::run(x, k, t);
+        }
+    }
+};
+
 template <int R>
 __global__ void __launch_bounds__(kThreads)
-    k_rowscale(uint8_t *dst, const uint8_t *src, size_t S, const uint16_t *__restrict__ coef, int skip_zero)
+    k_rowscale(uint8_t *dst, const uint8_t *src, size_t S, uint32_t rows, const uint16_t *__restrict__ coef,
+               int skip_zero)
 {
-    __shared__ __align__(16) uint8_t T[FT<R>::rec_bytes];
-    const uint32_t row = blockIdx.x;
-    const uint32_t c = coef[row];
-    if (c == 0) { // erased row of Phi: zero it without reading it
-        if (skip_zero) return;
-        uint4 *d4 = reinterpret_cast<uint4 *>(dst + (size_t)row * S);
-        for (size_t v = threadIdx.x; v < S / 16; v += blockDim.x) d4[v] = make_uint4(0, 0, 0, 0);
-        return;
+    __shared__ __align__(128) uint8_t T[kRowsPerCta * FT<R>::rec_bytes];
+    __shared__ uint32_t ks[kRowsPerCta];
+    const uint32_t r0 = blockIdx.x * kRowsPerCta;
+    constexpr uint32_t cpr = FT<R>::rec_bytes / 16;
+    for (uint32_t v = threadIdx.x; v < kRowsPerCta * cpr; v += blockDim.x) {
+        const uint32_t q = v / cpr, c = v - q * cpr;
+        const uint32_t k = r0 + q < rows ? coef[r0 + q] : 0u;
+        *reinterpret_cast<uint4 *>(T + rec_dst<R>(kRowsPerCta, q, c)) = rec_chunk<R>(k, c);
+        if (c == 0) ks[q] = k;
     }
-    for (uint32_t idx = threadIdx.x; idx < FT<R>::rec_entries; idx += blockDim.x)
-        rec_store<R>(T, idx, rec_entry<R>(c, idx));
     __syncthreads();
-    const uint4 *s4 = reinterpret_cast<const uint4 *>(src + (size_t)row * S);
-    uint4 *d4 = reinterpret_cast<uint4 *>(dst + (size_t)row * S);
-    for (size_t v = threadIdx.x; v < S / 16; v += blockDim.x) {
-        uint4 x = s4[v];
-        x.x = mul_word<R>(x.x, T);
-        x.y = mul_word<R>(x.y, T);
-        x.z = mul_word<R>(x.z, T);
-        x.w = mul_word<R>(x.w, T);
-        d4[v] = x;
+    uint32_t k[kRowsPerCta];
+#pragma unroll
+    for (uint32_t q = 0; q < kRowsPerCta; q++) k[q] = ks[q];
+    const TabRef<R> t = tab_ref<R>((uint32_t)__cvta_generic_to_shared(T), 0, kRowsPerCta);
+    const size_t vpr = S / 16;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src) + (size_t)r0 * vpr;
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst) + (size_t)r0 * vpr;
+    for (size_t i = threadIdx.x; i < vpr; i += blockDim.x) {
+        uint4 x[kRowsPerCta];
+#pragma unroll
+        for (uint32_t q = 0; q < kRowsPerCta; q++) x[q] = k[q] ? s4[q * vpr + i] : make_uint4(0, 0, 0, 0);
+        RowsScale<R>::run(x, k, t);
+#pragma unroll
+        for (uint32_t q = 0; q < kRowsPerCta; q++)
+            if (r0 + q < rows && (k[q] || !skip_zero)) d4[q * vpr + i] = x[q];
     }
 }
 
@@ -1017,10 +1087,11 @@ cudaError_t launch_rowscale(int r, uint8_t *dst, const uint8_t *src, size_t S, u
                             const uint16_t *coef, int skip_zero, cudaStream_t s, uint64_t *launches)
 {
     if (rows == 0) return cudaSuccess;
+    const uint32_t ctas = (rows + kRowsPerCta - 1) / kRowsPerCta;
     if (r == 8)
-        k_rowscale<8><<<rows, kThreads, 0, s>>>(dst, src, S, coef, skip_zero);
+        k_rowscale<8><<<ctas, kThreads, 0, s>>>(dst, src, S, rows, coef, skip_zero);
     else
-        k_rowscale<16><<<rows, kThreads, 0, s>>>(dst, src, S, coef, skip_zero);
+        k_rowscale<16><<<ctas, kThreads, 0, s>>>(dst, src, S, rows, coef, skip_zero);
     *launches += 1;
     return cudaGetLastError();
 }
