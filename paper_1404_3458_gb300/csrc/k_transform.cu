@@ -256,15 +256,64 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// One CTA per SM: the factor records of a row group stay in shared memory
-// while the CTA walks its column tiles; tile t+1 is copied in (cp.async)
-// while tile t is transformed.
+// Shared-memory offset of chunk c (16 bytes) of record q among nrec records
+// in the region layout of TabRef.
+template <int R> __device__ __forceinline__ uint32_t rec_dst(uint32_t nrec, uint32_t q, uint32_t c)
+{
+    if constexpr (R == 16)
+        return c < 8 ? (q << 7) + (c << 4) : (c < 16 ? ((nrec + q) << 7) + ((c - 8) << 4) : (nrec << 8) + (q << 5) + ((c - 16) << 4));
+    else
+        return (q << 8) + (c << 4);
+}
+
+// Copy the factor records of the row group at hibase (levels [L0, L0+nlev))
+// into the region layout at tab (cp.async; the caller commits).
+template <int R>
+__device__ __forceinline__ void stage_pass_recs(const PassArgs &a, uint32_t nrows, uint32_t hibase, uint8_t *tab)
+{
+    const uint32_t nrec = nrows - 1;
+    constexpr uint32_t cpr = FT<R>::rec_bytes / 16;
+    for (uint32_t v = threadIdx.x; v < nrec * cpr; v += blockDim.x) {
+        const uint32_t q = v / cpr, c = v - q * cpr;
+        uint32_t s = 0;
+        while (q >= rec_base(nrows, s + 1)) s++;
+        const uint32_t beta = q - rec_base(nrows, s);
+        const uint32_t i = a.L0 + s;
+        const uint32_t y = ((hibase | (beta << (i + 1))) ^ a.l) >> i;
+        const uint8_t *src = a.rec + (size_t)(level_off(R, i) + y) * FT<R>::rec_bytes + c * 16;
+        cp_async16(tab + rec_dst<R>(nrec, q, c), src);
+    }
+}
+
+// The levels of one tile in shared memory: register rounds of <= 4 levels.
+template <int R, int INV>
+__device__ __forceinline__ void pass_tile(uint32_t sdata, uint32_t stab, uint32_t nlev, uint32_t lg_w)
+{
+    const uint32_t nrows = 1u << nlev, nrec = nrows - 1;
+    const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, qb = nlev - qa;
+    if (INV) {
+        run_round<R, INV>(qa, sdata, stab, nrec, nrows, lg_w, 0);
+        if (qb) {
+            __syncthreads();
+            run_round<R, INV>(qb, sdata, stab, nrec, nrows, lg_w, qa);
+        }
+    } else {
+        if (qb) {
+            run_round<R, INV>(qb, sdata, stab, nrec, nrows, lg_w, qa);
+            __syncthreads();
+        }
+        run_round<R, INV>(qa, sdata, stab, nrec, nrows, lg_w, 0);
+    }
+}
+
+// One CTA walks the column tiles [y0, y0 + ystep, ...) of row group g: the
+// group's factor records stay in shared memory; tile t+1 is copied in
+// (cp.async) while tile t is transformed.
 template <int R, int INV>
 __device__ __forceinline__ void pass_body(const PassArgs &a, uint32_t lg_cw, uint32_t g, uint32_t y0, uint32_t ystep,
                                           uint8_t *sm)
 {
     const uint32_t nlev = a.nlev, nrows = 1u << nlev, nrec = nrows - 1;
-    uint8_t *tab = sm;
     const uint32_t stab = (uint32_t)__cvta_generic_to_shared(sm);
     const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
     uint8_t *const buf0 = sm + tab_bytes<R>(nrec);
@@ -275,24 +324,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, uint32_t lg_cw, uin
     const size_t col0 = (size_t)y0 << lg_cw;
     const uint32_t ntiles = col0 < a.S ? (uint32_t)((a.S - col0 + col_step - 1) / col_step) : 0;
 
-    // Stage the factor records of this row group (first copy group).
-    constexpr uint32_t cpr = FT<R>::rec_bytes / 16;
-    for (uint32_t v = threadIdx.x; v < nrec * cpr; v += blockDim.x) {
-        const uint32_t q = v / cpr, c = v - q * cpr;
-        uint32_t s = 0;
-        while (q >= rec_base(nrows, s + 1)) s++;
-        const uint32_t beta = q - rec_base(nrows, s);
-        const uint32_t i = a.L0 + s;
-        const uint32_t y = ((hibase | (beta << (i + 1))) ^ a.l) >> i;
-        const uint8_t *src = a.rec + (size_t)(level_off(R, i) + y) * FT<R>::rec_bytes + c * 16;
-        uint32_t dst;
-        if constexpr (R == 16)
-            dst = c < 8 ? (q << 7) + (c << 4)
-                        : (c < 16 ? ((nrec + q) << 7) + ((c - 8) << 4) : (nrec << 8) + (q << 5) + ((c - 16) << 4));
-        else
-            dst = (q << 8) + (c << 4);
-        cp_async16(tab + dst, src);
-    }
+    stage_pass_recs<R>(a, nrows, hibase, sm); // first copy group
 
     auto issue = [&](uint32_t t, uint32_t *dstbuf) {
         const size_t col = col0 + (size_t)t * col_step;
@@ -312,25 +344,12 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, uint32_t lg_cw, uin
     if (ntiles > 1) issue(1, reinterpret_cast<uint32_t *>(buf0 + tile_bytes));
     cp_async_commit();
 
-    const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, qb = nlev - qa;
     for (uint32_t t = 0; t < ntiles; t++) {
         uint32_t *data = reinterpret_cast<uint32_t *>(buf0 + (t & 1u) * tile_bytes);
         const uint32_t sdata = (uint32_t)__cvta_generic_to_shared(data);
         cp_async_wait1(); // tile t (and the records) have landed for this thread
         __syncthreads();
-        if (INV) {
-            run_round<R, INV>(qa, sdata, stab, nrec, nrows, lg_w, 0);
-            if (qb) {
-                __syncthreads();
-                run_round<R, INV>(qb, sdata, stab, nrec, nrows, lg_w, qa);
-            }
-        } else {
-            if (qb) {
-                run_round<R, INV>(qb, sdata, stab, nrec, nrows, lg_w, qa);
-                __syncthreads();
-            }
-            run_round<R, INV>(qa, sdata, stab, nrec, nrows, lg_w, 0);
-        }
+        pass_tile<R, INV>(sdata, stab, nlev, lg_w);
         __syncthreads();
         {
             const size_t col = col0 + (size_t)t * col_step;
@@ -358,6 +377,79 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(PassArgs a, uint32_t l
 {
     extern __shared__ __align__(128) uint8_t sm[];
     pass_body<R, INV>(a, lg_cw, blockIdx.x, blockIdx.y, gridDim.y, sm);
+}
+
+// Persistent form: one CTA per SM takes a contiguous range of the
+// (row group, column tile) items in group-major order.  Two record buffers
+// and two tile buffers: the records of the next group and the tile after
+// next are copied in while the current tile is transformed.  Needs at least
+// two tiles per group (then at most two groups are live at a time).
+template <int R, int INV>
+__global__ void __launch_bounds__(kPassThreads, 1) k_pass_p(PassArgs a, uint32_t lg_cw, uint32_t ntiles, uint32_t items)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
+    const uint32_t nlev = a.nlev, nrows = 1u << nlev, nrec = nrows - 1;
+    const uint32_t tab_sz = tab_bytes<R>(nrec);
+    const uint32_t stab0 = (uint32_t)__cvta_generic_to_shared(sm);
+    const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
+    uint8_t *const buf0 = sm + 2 * tab_sz;
+    const uint32_t tile_bytes = nrows << lg_cw;
+    const uint32_t i0 = (uint32_t)((uint64_t)blockIdx.x * items / gridDim.x);
+    const uint32_t i1 = (uint32_t)((uint64_t)(blockIdx.x + 1) * items / gridDim.x);
+    if (i0 >= i1) return;
+    const uint32_t g_first = i0 / ntiles;
+
+    // tile of item k into dstbuf, with its group's records when k opens a group
+    auto issue = [&](uint32_t k, uint8_t *dstbuf) {
+        const uint32_t g = k / ntiles, t = k - g * ntiles;
+        const uint32_t lo = g & ((1u << a.L0) - 1u);
+        const uint32_t hibase = (g >> a.L0) << (a.L0 + nlev);
+        if (k == i0 || t == 0) stage_pass_recs<R>(a, nrows, hibase, sm + ((g - g_first) & 1u) * tab_sz);
+        const size_t col = (size_t)t << lg_cw;
+        const size_t rem = a.S - col;
+        const uint32_t width = rem < cw ? (uint32_t)rem : cw;
+        for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
+            const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
+            if (c * 16 < width) {
+                const size_t row = hibase | ((size_t)m << a.L0) | lo;
+                cp_async16(dstbuf + v * 16, a.src + row * a.S + col + c * 16);
+            }
+        }
+    };
+
+    issue(i0, buf0);
+    cp_async_commit();
+    if (i0 + 1 < i1) issue(i0 + 1, buf0 + tile_bytes);
+    cp_async_commit();
+
+    for (uint32_t k = i0; k < i1; k++) {
+        uint8_t *data = buf0 + ((k - i0) & 1u) * tile_bytes;
+        const uint32_t sdata = (uint32_t)__cvta_generic_to_shared(data);
+        const uint32_t g = k / ntiles, t = k - g * ntiles;
+        cp_async_wait1(); // item k's tile and records have landed for this thread
+        __syncthreads();
+        pass_tile<R, INV>(sdata, stab0 + ((g - g_first) & 1u) * tab_sz, nlev, lg_w);
+        __syncthreads();
+        {
+            const uint32_t lo = g & ((1u << a.L0) - 1u);
+            const uint32_t hibase = (g >> a.L0) << (a.L0 + nlev);
+            const size_t col = (size_t)t << lg_cw;
+            const size_t rem = a.S - col;
+            const uint32_t width = rem < cw ? (uint32_t)rem : cw;
+            for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
+                const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
+                if (c * 16 < width) {
+                    const size_t row = hibase | ((size_t)m << a.L0) | lo;
+                    *reinterpret_cast<uint4 *>(a.dst + row * a.S + col + c * 16) =
+                        reinterpret_cast<const uint4 *>(data)[v];
+                }
+            }
+        }
+        __syncthreads(); // everyone has read this tile and this group's records
+        if (k + 2 < i1) issue(k + 2, data);
+        cp_async_commit();
+    }
+    cp_async_wait_all();
 }
 
 __global__ void __launch_bounds__(kThreads) k_superset(SupersetArgs a, uint32_t lg_cw)
@@ -423,15 +515,6 @@ __global__ void __launch_bounds__(kThreads) k_superset(SupersetArgs a, uint32_t 
 // derivative thus multiplies twice per element, and each pass holds one set
 // of 2^nlev records.
 
-// Shared-memory offset of chunk c (16 bytes) of record q among nrec records
-// in the region layout of TabRef.
-template <int R> __device__ __forceinline__ uint32_t rec_dst(uint32_t nrec, uint32_t q, uint32_t c)
-{
-    if constexpr (R == 16)
-        return c < 8 ? (q << 7) + (c << 4) : (c < 16 ? ((nrec + q) << 7) + ((c - 8) << 4) : (nrec << 8) + (q << 5) + ((c - 16) << 4));
-    else
-        return (q << 8) + (c << 4);
-}
 
 // x[U] *= the constant of record (base | U << S0), U < N; t refers to base.
 template <int R, int N, int S0, int U = 0> struct RowMul {
@@ -769,9 +852,23 @@ template <int R, int INV>
 cudaError_t pass_impl(const PassArgs &a, cudaStream_t s)
 {
     const uint32_t nrows = 1u << a.nlev;
-    const uint32_t lg_cw = a.lg_cw ? a.lg_cw : pick_lg_cw(nrows, a.S);
-    const size_t smem = tab_bytes<R>(nrows - 1) + (2 * (size_t)nrows << lg_cw);
+    uint32_t lg_cw = a.lg_cw ? a.lg_cw : pick_lg_cw(nrows, a.S);
+    const size_t tab = tab_bytes<R>(nrows - 1);
     const uint32_t ngroups = a.h >> a.nlev;
+    // persistent form: two record sets, at least two tiles per group
+    while (lg_cw > 4 && 2 * tab + (2 * (size_t)nrows << lg_cw) > kPassSmem) lg_cw--;
+    const size_t ntiles_p = (a.S + (1ull << lg_cw) - 1) >> lg_cw;
+    if (ntiles_p >= 2 && 2 * tab + (2 * (size_t)nrows << lg_cw) <= kPassSmem) {
+        const uint64_t items = (uint64_t)ngroups * ntiles_p;
+        if (items < (1ull << 32)) {
+            const uint32_t ctas = (uint32_t)std::min<uint64_t>(items, kSms);
+            const size_t smem = 2 * tab + (2 * (size_t)nrows << lg_cw);
+            k_pass_p<R, INV><<<ctas, kPassThreads, smem, s>>>(a, lg_cw, (uint32_t)ntiles_p, (uint32_t)items);
+            return cudaGetLastError();
+        }
+    }
+    lg_cw = a.lg_cw ? a.lg_cw : pick_lg_cw(nrows, a.S);
+    const size_t smem = tab + (2 * (size_t)nrows << lg_cw);
     const size_t ntiles = (a.S + (1ull << lg_cw) - 1) >> lg_cw;
     // About 4 tiles per CTA and at least ~6 CTAs per SM in total.
     size_t y = (ntiles + 3) / 4;
@@ -975,6 +1072,10 @@ cudaError_t configure_transform_kernels()
     if ((e = cudaFuncSetAttribute(k_pass<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_pass<16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_pass<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv<8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
@@ -996,10 +1097,10 @@ uint32_t plan_deriv_lg_cw(int r, uint32_t nlev, int mode, size_t S, bool batch)
 
 uint32_t max_lg_cw(int r, uint32_t nlev, size_t S)
 {
-    const size_t budget = kPassSmem;
+    // the persistent pass keeps two record sets
     const size_t tab = r == 16 ? tab_bytes<16>((1u << nlev) - 1) : tab_bytes<8>((1u << nlev) - 1);
     uint32_t lg = 4;
-    while (lg < 12 && tab + (2ull << nlev << (lg + 1)) <= budget && (1ull << (lg + 1)) < 2 * S) lg++;
+    while (lg < 12 && 2 * tab + (2ull << nlev << (lg + 1)) <= kPassSmem && (1ull << (lg + 1)) < 2 * S) lg++;
     return lg;
 }
 

@@ -28,7 +28,7 @@ def plans_for(r, lgh, S):
     splits = [lgh] if lgh <= 8 else [a for a in range(1, 9) if 1 <= lgh - a <= 8]
     for a in splits:
         b = lgh - a
-        for lo, hi in ((4, 4 if b else 0), (6, 8 if b else 0)):
+        for lo, hi in ((4, 4 if b else 0), (6, 6 if b else 0)):
             cap = max(4, int(np.ceil(np.log2(S))))
             out.append({"split": a, "lg_tile_low": min(lo, cap), "lg_tile_high": min(hi, cap) if b else 0})
     return out
