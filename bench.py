@@ -433,6 +433,7 @@ def run_serving(ctx, torch, args, rank):
             torch.cuda.synchronize()
             if name == "served":
                 srv = SV.Server(ctx, budget, max_inflight=2, max_batch=1024)
+                srv.prewarm([(r, n, k, S) for (r, n, k, S, e) in specs])
                 st = srv.run(reqs)
                 del srv
             else:

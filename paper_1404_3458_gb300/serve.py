@@ -6,13 +6,17 @@ Poisson stream) and are served on one GPU:
 * admission: a request is admitted only when its codeword buffer and its
   share of batch scratch fit in a device-memory budget (an arena carved once
   from the device; nothing is allocated per request);
-* continuous batching: whenever a launch slot is free, every admitted request
-  that has not started yet is planned into one batch per operation
-  (lch_batch_create_in, memory from the arena) and launched as a single
-  persistent kernel, while up to `max_inflight` earlier batches are still
-  running on other streams;
-* retirement: completed batches are detected by polling their CUDA events;
-  their requests get a completion time and their arena memory is released.
+* direct calls: while fewer than `max_direct` of them are in flight, a waiting
+  request is launched at once as its own rs_encode/rs_decode call on a
+  stream of its own, so a lightly loaded server answers as fast as one call;
+* continuous batching: once that stream is full and at least `min_batch`
+  requests wait, a free launch slot takes every admitted request that has not
+  started yet and plans it into one batch per operation (lch_batch_create_in,
+  memory from the arena), launched as a single persistent kernel while up to
+  `max_inflight` earlier batches are still running on other streams;
+* retirement: completed calls and batches are detected by polling their CUDA
+  events; their requests get a completion time and their arena memory is
+  released.
 
 `serve_plain` is the reference policy: the same arrivals and budget, but each
 request is its own rs_encode/rs_decode call on one stream.
@@ -114,7 +118,8 @@ class _Inflight:
 
 
 class Server:
-    def __init__(self, ctx: "lch.Context", budget_bytes: int, max_inflight: int = 3, max_batch: int = 1024):
+    def __init__(self, ctx: "lch.Context", budget_bytes: int, max_inflight: int = 3, max_batch: int = 1024,
+                 min_batch: int = 16, max_direct: int = 32):
         import torch
 
         self.torch = torch
@@ -123,11 +128,34 @@ class Server:
         self.mem = torch.empty(budget_bytes, dtype=torch.uint8, device="cuda")
         self.max_inflight = max_inflight
         self.max_batch = max_batch
+        self.min_batch = min_batch
+        self.max_direct = max_direct
         self.streams = [torch.cuda.Stream() for _ in range(max_inflight)]
         # A lone request skips batch planning and runs as a single-codeword
         # call; each launch slot has its own context so those calls never
         # share context scratch across streams.
         self.slot_ctx = [lch.Context(ctx.device) for _ in range(max_inflight)]
+        # direct calls: one stream and one context of their own
+        self.direct_stream = torch.cuda.Stream()
+        self.direct_ctx = lch.Context(ctx.device)
+
+    def prewarm(self, shapes):
+        """Build, before serving, what each context builds on first use for
+        these (field, n, k, shard_bytes) shapes: field tables, FWHT(log)
+        tables, shortened-code locators and scratch of the largest size (a
+        first use synchronises the device, which would stall the loop)."""
+        torch = self.torch
+        seen = sorted(set(shapes), key=lambda t: t[1] * t[3], reverse=True)
+        for field, n, k, S in seen:
+            buf = torch.zeros((n, S), dtype=torch.uint8, device="cuda")
+            mask = np.zeros(n, dtype=np.uint8)
+            mask[k:] = 1
+            for c in [self.ctx, self.direct_ctx] + self.slot_ctx:
+                c.rs_encode(n, k, field, buf)
+                if k < n:
+                    c.rs_decode(n, k, field, buf, mask)
+            del buf
+        torch.cuda.synchronize()
 
     def _view(self, off: int, n: int, S: int):
         return self.mem[off:off + n * S].view(n, S)
@@ -186,14 +214,44 @@ class Server:
         pending = deque(sorted(requests, key=lambda q: q.arrival))
         waiting: deque = deque()
         inflight: list = []
+        direct: deque = deque()  # (event, request) of direct calls, in launch order
         free_slots = list(range(self.max_inflight))
         batches_launched = 0
+        direct_launched = 0
         blocked = False  # admitted work did not fit: wait for a retirement
         t0 = clock()
-        while pending or waiting or inflight:
+        while pending or waiting or inflight or direct:
             now = clock() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
+            # retire completed direct calls (one stream: in order)
+            while direct and direct[0][0].query():
+                _, r = direct.popleft()
+                r.done = clock() - t0
+                if on_done is not None:
+                    on_done(r)
+                self._release(r)
+                blocked = False
+            # launch waiting requests one by one while the direct stream has room
+            while waiting and len(direct) < self.max_direct and not blocked:
+                r = waiting[0]
+                if _estimate(r) > self.arena.size - self.arena.used or not self._admit(r):
+                    if not inflight and not direct and _estimate(r) > self.arena.size:
+                        raise RuntimeError("a request does not fit in the serving memory budget")
+                    break
+                waiting.popleft()
+                r.admitted = clock() - t0
+                with torch.cuda.stream(self.direct_stream):
+                    if r.payload is not None:
+                        r.buf.copy_(r.payload, non_blocking=True)
+                    if r.op == lch.BATCH_ENCODE:
+                        self.direct_ctx.rs_encode(r.n, r.k, r.field, r.buf, stream=self.direct_stream)
+                    else:
+                        self.direct_ctx.rs_decode(r.n, r.k, r.field, r.buf, r.mask, stream=self.direct_stream)
+                    ev = torch.cuda.Event()
+                    ev.record(self.direct_stream)
+                direct.append((ev, r))
+                direct_launched += 1
             # retire completed batches
             still = []
             for f in inflight:
@@ -215,7 +273,10 @@ class Server:
                     still.append(f)
             inflight = still
             # admit whatever fits and launch it as one batch per operation
-            if waiting and free_slots and not blocked:
+            # (fewer than min_batch also go out as a batch once no more arrive
+            # and the direct stream is full)
+            enough = len(waiting) >= self.min_batch or (waiting and not pending and len(direct) >= self.max_direct)
+            if enough and free_slots and not blocked:
                 slot = free_slots[-1]
                 stream = self.streams[slot]
                 admitted = []
@@ -226,7 +287,7 @@ class Server:
                         break
                     room -= need
                     admitted.append(waiting.popleft())
-                if not admitted and waiting and not inflight and _estimate(waiting[0]) > self.arena.size:
+                if not admitted and waiting and not inflight and not direct and _estimate(waiting[0]) > self.arena.size:
                     raise RuntimeError("a request does not fit in the serving memory budget")
                 if admitted:
                     f = _Inflight(event=torch.cuda.Event(), slot=slot, batches=[], requests=[])
@@ -253,7 +314,7 @@ class Server:
                         waiting.appendleft(r)
                     if back:
                         blocked = True
-                        if not inflight and not f.requests:
+                        if not inflight and not direct and not f.requests:
                             raise RuntimeError("a request does not fit in the serving memory budget")
                     if f.requests:
                         for r in f.requests:
@@ -262,12 +323,15 @@ class Server:
                         f.event.record(stream)
                         inflight.append(f)
                     continue
-            if not inflight and not waiting and pending:
+            if not inflight and not direct and not waiting and pending:
                 # idle until the next arrival
                 wait = pending[0].arrival - (clock() - t0)
                 if wait > 0:
                     time.sleep(min(wait, 1e-3))
-        return _stats(requests, batches_launched)
+        st = _stats(requests, batches_launched + direct_launched)
+        st["batches"] = batches_launched
+        st["direct_calls"] = direct_launched
+        return st
 
 
 def serve_plain(ctx: "lch.Context", requests: list, budget_bytes: int, clock=time.perf_counter, on_done=None) -> dict:

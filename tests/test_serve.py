@@ -62,21 +62,25 @@ def _requests(ctx, count, rate, seed):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("budget_mb,rate", [(64, 20000.0), (8, 200000.0)])
-def test_served_results_equal_alone(ctx, budget_mb, rate):
+@pytest.mark.parametrize("budget_mb,rate,min_batch,max_direct", [(64, 20000.0, 16, 4), (8, 200000.0, 16, 4),
+                                                                  (64, 200000.0, 2, 0), (16, 50000.0, 4, 1)])
+def test_served_results_equal_alone(ctx, budget_mb, rate, min_batch, max_direct):
     import torch
 
-    reqs, expect = _requests(ctx, 60, rate, seed=budget_mb)
+    reqs, expect = _requests(ctx, 60, rate, seed=budget_mb + min_batch)
     got = {}
-    server = SV.Server(ctx, budget_mb << 20, max_inflight=2, max_batch=32)
+    server = SV.Server(ctx, budget_mb << 20, max_inflight=2, max_batch=32, min_batch=min_batch,
+                       max_direct=max_direct)
     stats = server.run(reqs, on_done=lambda r: got.__setitem__(r.rid, r.buf.clone()))
     torch.cuda.synchronize()
     assert len(got) == len(reqs)
     for r, e in zip(reqs, expect):
         assert torch.equal(got[r.rid], e), (r.rid, r.op, r.n, r.k, r.shard_bytes)
     assert stats["requests"] == 60 and stats["p99_ms"] >= stats["p50_ms"] > 0
-    # several requests were served by one launch (continuous batching)
-    assert stats["launch_groups"] < len(reqs)
+    assert stats["batches"] + stats["direct_calls"] == stats["launch_groups"]
+    if max_direct == 0:
+        # everything went out in batches, several requests per launch
+        assert stats["direct_calls"] == 0 and stats["batches"] < len(reqs)
 
 
 @pytest.mark.gpu
