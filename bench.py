@@ -39,6 +39,14 @@ import numpy as np  # noqa: E402
 from paper_1404_3458_gb300 import workloads as WL  # noqa: E402
 
 METRIC = "encode/decode GB/s of shard data"
+
+# DRAM read + write bytes of one k_pass_p launch of the decoder's inverse
+# transform (h = 65536, 4 KiB shards): the mean of its two passes in one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum), beside that
+# launch's algorithmic bytes 2 h S.  Valid for the kernel as profiled;
+# re-measure after changing it.
+KPASS_TRAFFIC = {"bytes": 495810432, "alg_bytes": 2 * 65536 * 4096,
+                 "launch": "k_pass_p<16,1> decoder inverse transform, h=65536, S=4096 (ncu)"}
 UNIT = "GB/s"
 
 
@@ -277,7 +285,8 @@ def run_ours(args):
                 "peak": round(alu_peak, 2), "unit": "Gmul/s", "frac": round(achieved_mul / alu_peak, 4),
                 "peak_source": (f"derived: 152 SMs x 64 ALU lanes/clk x {sm_mhz:.0f} MHz / 8.5 ALU ops per "
                                 "GF(2^16) split-table multiply-add"),
-                "traffic": None, "launches_per_step": d["launches"] / args.steps,
+                "traffic": KPASS_TRAFFIC["bytes"], "traffic_alg_bytes": KPASS_TRAFFIC["alg_bytes"],
+                "traffic_launch": KPASS_TRAFFIC["launch"], "launches_per_step": d["launches"] / args.steps,
                 "share_of_kernel_time": round(d["ms"] / tot_ms, 4) if tot_ms else None,
                 "hbm": {"achieved": round(achieved_gbs, 2), "peak": hbm, "unit": "GB/s",
                         "frac": round(achieved_gbs / hbm, 4), "peak_source": f"{hbm_src} hbm_gbs"}}

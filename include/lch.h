@@ -54,6 +54,7 @@ extern "C" {
 #define LCH_ETOOMANY 2 /* rs_decode: more than n - k erasures */
 #define LCH_ENOMEM 3   /* device or host allocation failed */
 #define LCH_ECUDA 4    /* a CUDA runtime call failed (see lch_last_error) */
+#define LCH_ETIMEDOUT 5 /* a batch task gave up waiting for its predecessors */
 
 /* Fields. */
 #define LCH_GF8 8
@@ -195,10 +196,23 @@ LCH_API int lch_batch_create_in(lch_ctx *ctx, int op, const lch_codeword *cws, u
 LCH_API int lch_batch_run(lch_ctx *ctx, lch_batch *batch, void *stream);
 
 /* Wait for the stream of the batch's last run and report whether that run
- * completed: LCH_OK, or LCH_ECUDA if a task gave up waiting for its
+ * completed: LCH_OK, or LCH_ETIMEDOUT if a task gave up waiting for its
  * predecessors (the kernel then drains without finishing; the outputs are
- * undefined). */
+ * undefined; the context and the batch stay usable). */
 LCH_API int lch_batch_status(lch_ctx *ctx, lch_batch *batch);
+
+/* How long one task of a batch run may wait for the tasks it depends on
+ * before the run gives up (default 2 s; applies to runs enqueued later).
+ * Every wait of the persistent kernel polls a completion counter and stops at
+ * this limit, so a run never spins forever.  LCH_EINVAL for 0. */
+LCH_API int lch_batch_set_wait_limit(lch_ctx *ctx, uint32_t wait_us);
+
+/* Failure-path self-test (the paper has no counterpart): runs the batch
+ * kernel on a one-task plan whose dependency is never met, so its wait must
+ * give up after the context's wait limit.  Synchronises `stream`.  Returns
+ * LCH_ETIMEDOUT when the wait gave up as designed (the expected result),
+ * LCH_OK never, LCH_ENOMEM or LCH_ECUDA on other failures. */
+LCH_API int lch_batch_selftest_stall(lch_ctx *ctx, void *stream);
 
 /* Number of tasks in the plan (diagnostics). */
 LCH_API uint32_t lch_batch_tasks(const lch_batch *batch);

@@ -972,7 +972,14 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
     return v;
 }
 
-constexpr uint32_t kMaxWaitSpins = 1u << 24; // ~1-2 s with the back-off below
+constexpr uint32_t kMaxWaitSpins = 1u << 24; // backstop beside the time limit (<= ~17 s with the back-off)
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Shared memory of a batch task body (the largest: a derivative pass with
 // 2 x 256 GF(2^16) records and 2 stages of 2 tiles; tiles are narrowed to fit).
@@ -981,7 +988,7 @@ __host__ __device__ constexpr size_t batch_body_smem() { return 192 * 1024; }
 // The persistent batch kernel: one CTA per SM pulls tasks in queue order.
 __global__ void __launch_bounds__(kPassThreads, 1)
     k_batch(const BatchOp *__restrict__ ops, const BatchTask *__restrict__ tasks, uint32_t ntasks,
-            BatchCounters *ctr, uint32_t *done)
+            BatchCounters *ctr, uint32_t *done, uint64_t wait_ns)
 {
     // No static shared variables: the bodies address their tables with
     // (index | base), which needs the dynamic region to start 128-byte aligned.
@@ -999,10 +1006,11 @@ __global__ void __launch_bounds__(kPassThreads, 1)
         const BatchTask t = tasks[ti];
         if (threadIdx.x == 0 && t.need) {
             uint32_t spins = 0, ns = 32;
+            const uint64_t t0 = global_ns();
             while (ld_acquire(done + t.cw) < t.need) {
                 __nanosleep(ns);
                 if (ns < 1024) ns <<= 1;
-                if (++spins > kMaxWaitSpins) { // give up: flag it and let every CTA drain
+                if (++spins > kMaxWaitSpins || global_ns() - t0 > wait_ns) { // give up: flag it, let every CTA drain
                     atomicOr(&ctr->err, 1u);
                     s_abort = 1;
                     break;
@@ -1134,9 +1142,9 @@ cudaError_t launch_fill(uint8_t *p, size_t bytes, cudaStream_t s)
 size_t batch_smem_bytes() { return batch_body_smem() + 16; } // + the queue control words
 
 cudaError_t launch_batch(const BatchOp *ops, const BatchTask *tasks, uint32_t ntasks, BatchCounters *counters,
-                         uint32_t *done, uint32_t ctas, cudaStream_t s, uint64_t *launches)
+                         uint32_t *done, uint32_t ctas, uint64_t wait_ns, cudaStream_t s, uint64_t *launches)
 {
-    k_batch<<<ctas, kPassThreads, batch_smem_bytes(), s>>>(ops, tasks, ntasks, counters, done);
+    k_batch<<<ctas, kPassThreads, batch_smem_bytes(), s>>>(ops, tasks, ntasks, counters, done, wait_ns);
     *launches += 1;
     return cudaGetLastError();
 }

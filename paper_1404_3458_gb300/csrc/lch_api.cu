@@ -17,6 +17,7 @@ using namespace lch;
 
 struct lch_ctx {
     int device = 0;
+    uint64_t batch_wait_ns = 2000000000ull; // per-task dependency wait limit of batch runs
     FieldTables tab[2];          // [0]: GF(2^8), [1]: GF(2^16)
     uint32_t *fl[2][17] = {};    // FWHT of the log table per field and lg n
     uint8_t *scratch = nullptr;  // grows on demand
@@ -1032,7 +1033,8 @@ LCH_API int lch_batch_run(lch_ctx *ctx, lch_batch *b, void *stream)
     CU(cudaMemsetAsync(b->counters, 0, b->counter_bytes, s), "counter reset");
     BatchCounters *ctr = reinterpret_cast<BatchCounters *>(b->counters);
     uint32_t *done = reinterpret_cast<uint32_t *>(b->counters + sizeof(BatchCounters));
-    CU(launch_batch(b->ops, b->tasks, b->ntasks, ctr, done, b->ctas, s, &ctx->launches), "batch launch");
+    CU(launch_batch(b->ops, b->tasks, b->ntasks, ctr, done, b->ctas, ctx->batch_wait_ns, s, &ctx->launches),
+       "batch launch");
     return LCH_OK;
 }
 
@@ -1045,7 +1047,51 @@ LCH_API int lch_batch_status(lch_ctx *ctx, lch_batch *b)
     BatchCounters h{};
     CU(cudaMemcpyAsync(&h, b->counters, sizeof(h), cudaMemcpyDeviceToHost, b->last), "batch status");
     CU(cudaStreamSynchronize(b->last), "batch status");
-    if (h.err) return fail(LCH_ECUDA, "a batch task gave up waiting for its predecessors");
+    if (h.err) return fail(LCH_ETIMEDOUT, "a batch task gave up waiting for its predecessors");
+    return LCH_OK;
+}
+
+LCH_API int lch_batch_set_wait_limit(lch_ctx *ctx, uint32_t wait_us)
+{
+    if (!ctx) return fail(LCH_EINVAL, "ctx is NULL");
+    if (wait_us == 0) return fail(LCH_EINVAL, "wait_us must be positive");
+    ctx->batch_wait_ns = (uint64_t)wait_us * 1000ull;
+    return LCH_OK;
+}
+
+LCH_API int lch_batch_selftest_stall(lch_ctx *ctx, void *stream)
+{
+    if (!ctx) return fail(LCH_EINVAL, "ctx is NULL");
+    DeviceScope ds(ctx->device);
+    if (!ds.ok) return fail(LCH_ECUDA, "cannot select device %d", ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // one task over zero rows that waits for one completed task of its
+    // codeword; no task ever completes one, so the wait must give up
+    BatchOp op{};
+    op.type = kOpRows;
+    op.field = LCH_GF8;
+    op.S = 16;
+    BatchTask task{0, 0, 1, 0, 0};
+    const size_t ctr_bytes = sizeof(BatchCounters) + sizeof(uint32_t);
+    uint8_t *mem = nullptr;
+    if (cudaMalloc(&mem, 512 + ctr_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LCH_ENOMEM, "self-test allocation failed");
+    }
+    BatchOp *d_op = reinterpret_cast<BatchOp *>(mem);
+    BatchTask *d_task = reinterpret_cast<BatchTask *>(mem + 256);
+    BatchCounters *ctr = reinterpret_cast<BatchCounters *>(mem + 512);
+    uint32_t *done = reinterpret_cast<uint32_t *>(mem + 512 + sizeof(BatchCounters));
+    BatchCounters h{};
+    cudaError_t e = cudaMemcpyAsync(d_op, &op, sizeof(op), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_task, &task, sizeof(task), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, ctr_bytes, s);
+    if (e == cudaSuccess) e = launch_batch(d_op, d_task, 1, ctr, done, 1, ctx->batch_wait_ns, s, &ctx->launches);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(mem);
+    if (e != cudaSuccess) return cuda_fail(e, "batch self-test");
+    if (h.err) return fail(LCH_ETIMEDOUT, "a batch task gave up waiting for its predecessors");
     return LCH_OK;
 }
 
@@ -1067,6 +1113,7 @@ LCH_API const char *lch_strerror(int status)
     case LCH_ETOOMANY: return "more erasures than n - k";
     case LCH_ENOMEM: return "out of memory";
     case LCH_ECUDA: return "CUDA error";
+    case LCH_ETIMEDOUT: return "a batch task gave up waiting";
     default: return "unknown status";
     }
 }

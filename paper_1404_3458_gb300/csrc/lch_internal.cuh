@@ -273,8 +273,10 @@ struct BatchCounters {
 };
 constexpr uint32_t kBatchMaxLgn = 13; // single-CTA locator per codeword
 size_t batch_smem_bytes();
+// wait_ns: how long one task may wait for its predecessors before the run
+// gives up (err set, every CTA drains).
 cudaError_t launch_batch(const BatchOp *ops, const BatchTask *tasks, uint32_t ntasks, BatchCounters *counters,
-                         uint32_t *done, uint32_t ctas, cudaStream_t s, uint64_t *launches);
+                         uint32_t *done, uint32_t ctas, uint64_t wait_ns, cudaStream_t s, uint64_t *launches);
 // Shared helpers of the planners.
 uint32_t plan_lg_cw(uint32_t nrows, size_t S);
 // Column tile width of a derivative pass of 2^nlev rows in mode `mode`, for

@@ -19,7 +19,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "liblch.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "lch.h")
 
-LCH_OK, LCH_EINVAL, LCH_ETOOMANY, LCH_ENOMEM, LCH_ECUDA = 0, 1, 2, 3, 4
+LCH_OK, LCH_EINVAL, LCH_ETOOMANY, LCH_ENOMEM, LCH_ECUDA, LCH_ETIMEDOUT = 0, 1, 2, 3, 4, 5
 GF8, GF16 = 8, 16
 
 _lib = None
@@ -91,6 +91,8 @@ def load() -> ctypes.CDLL:
         "lch_profile_read": (i, [vp, i, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
         "lch_autotune": (i, [vp, i, u32, sz, vp, ctypes.POINTER(Tuning)]),
+        "lch_batch_set_wait_limit": (i, [vp, u32]),
+        "lch_batch_selftest_stall": (i, [vp, vp]),
         "lch_tune_set": (i, [vp, i, u32, sz, ctypes.POINTER(Tuning)]),
     }
     for name, (res, args) in sigs.items():
@@ -237,6 +239,16 @@ class Context:
 
     def batch(self, op: int, codewords, mem=None, stream=None) -> "Batch":
         return Batch(self, op, codewords, mem=mem, stream=stream)
+
+    def batch_set_wait_limit(self, wait_us: int):
+        """lch_batch_set_wait_limit: per-task dependency wait limit of later
+        batch runs."""
+        _check(load().lch_batch_set_wait_limit(self._h, int(wait_us)))
+
+    def batch_selftest_stall(self, stream=None) -> int:
+        """lch_batch_selftest_stall: the status of a batch run whose one task
+        can never start (LCH_ETIMEDOUT when the wait gave up as designed)."""
+        return int(load().lch_batch_selftest_stall(self._h, _stream_handle(stream)))
 
     def batch_bytes(self, op: int, codewords) -> int:
         """Device bytes a batch of these codewords needs (lch_batch_bytes)."""

@@ -128,3 +128,33 @@ def test_batch_refusals(ctx):
     empty.run()
     empty.status()
     assert empty.tasks == 0
+
+
+def test_batch_wait_gives_up_and_context_recovers():
+    """Failure path of the persistent kernel: a task whose dependency is
+    never met waits at most the context's limit, the run reports
+    LCH_ETIMEDOUT, and the same context then runs a batch correctly."""
+    import time
+
+    import torch
+
+    c = lch.Context(0)
+    try:
+        c.batch_set_wait_limit(20000)  # 20 ms
+        t0 = time.perf_counter()
+        assert c.batch_selftest_stall() == lch.LCH_ETIMEDOUT
+        assert time.perf_counter() - t0 < 5.0
+        with pytest.raises(lch.LchError):
+            c.batch_set_wait_limit(0)
+        r, n, k, S = 16, 256, 128, 64
+        host = np.zeros((n, S), dtype=np.uint8)
+        host[:k] = WL.shards(k, S, seed=123)
+        d = to_dev(host)
+        b = c.batch(lch.BATCH_ENCODE, [(n, k, r, d, None)])
+        b.run()
+        b.status()
+        cols = elem_cols(S, r, 4, seed=2)
+        assert np.array_equal(elems(d.cpu().numpy(), r)[:, cols], O.rs_encode(r, n, k, elems(host, r, cols)))
+        torch.cuda.synchronize()
+    finally:
+        c.close()
