@@ -318,6 +318,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, uint32_t lg_cw, uin
     const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
     uint8_t *const buf0 = sm + tab_bytes<R>(nrec);
     const uint32_t tile_bytes = nrows << lg_cw;
+    g += a.g0;
     const uint32_t lo = g & ((1u << a.L0) - 1u);
     const uint32_t hibase = (g >> a.L0) << (a.L0 + nlev);
     const size_t col_step = (size_t)ystep << lg_cw;
@@ -333,7 +334,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, uint32_t lg_cw, uin
         for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
             const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
             if (c * 16 < width) {
-                const size_t row = hibase | ((size_t)m << a.L0) | lo;
+                const size_t row = (hibase | ((size_t)m << a.L0) | lo) & a.src_mask;
                 cp_async16(reinterpret_cast<uint8_t *>(dstbuf) + v * 16, a.src + row * a.S + col + c * 16);
             }
         }
@@ -397,11 +398,11 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_p(PassArgs a, uint32_t
     const uint32_t i0 = (uint32_t)((uint64_t)blockIdx.x * items / gridDim.x);
     const uint32_t i1 = (uint32_t)((uint64_t)(blockIdx.x + 1) * items / gridDim.x);
     if (i0 >= i1) return;
-    const uint32_t g_first = i0 / ntiles;
+    const uint32_t g_first = i0 / ntiles + a.g0;
 
     // tile of item k into dstbuf, with its group's records when k opens a group
     auto issue = [&](uint32_t k, uint8_t *dstbuf) {
-        const uint32_t g = k / ntiles, t = k - g * ntiles;
+        const uint32_t g = k / ntiles + a.g0, t = k - (k / ntiles) * ntiles;
         const uint32_t lo = g & ((1u << a.L0) - 1u);
         const uint32_t hibase = (g >> a.L0) << (a.L0 + nlev);
         if (k == i0 || t == 0) stage_pass_recs<R>(a, nrows, hibase, sm + ((g - g_first) & 1u) * tab_sz);
@@ -411,7 +412,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_p(PassArgs a, uint32_t
         for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
             const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
             if (c * 16 < width) {
-                const size_t row = hibase | ((size_t)m << a.L0) | lo;
+                const size_t row = (hibase | ((size_t)m << a.L0) | lo) & a.src_mask;
                 cp_async16(dstbuf + v * 16, a.src + row * a.S + col + c * 16);
             }
         }
@@ -425,7 +426,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_p(PassArgs a, uint32_t
     for (uint32_t k = i0; k < i1; k++) {
         uint8_t *data = buf0 + ((k - i0) & 1u) * tile_bytes;
         const uint32_t sdata = (uint32_t)__cvta_generic_to_shared(data);
-        const uint32_t g = k / ntiles, t = k - g * ntiles;
+        const uint32_t g = k / ntiles + a.g0, t = k - (k / ntiles) * ntiles;
         cp_async_wait1(); // item k's tile and records have landed for this thread
         __syncthreads();
         pass_tile<R, INV>(sdata, stab0 + ((g - g_first) & 1u) * tab_sz, nlev, lg_w);
@@ -854,7 +855,7 @@ cudaError_t pass_impl(const PassArgs &a, cudaStream_t s)
     const uint32_t nrows = 1u << a.nlev;
     uint32_t lg_cw = a.lg_cw ? a.lg_cw : pick_lg_cw(nrows, a.S);
     const size_t tab = tab_bytes<R>(nrows - 1);
-    const uint32_t ngroups = a.h >> a.nlev;
+    const uint32_t ngroups = a.ngroups ? a.ngroups : (a.h >> a.nlev) - a.g0;
     // persistent form: two record sets, at least two tiles per group
     while (lg_cw > 4 && 2 * tab + (2 * (size_t)nrows << lg_cw) > kPassSmem) lg_cw--;
     const size_t ntiles_p = (a.S + (1ull << lg_cw) - 1) >> lg_cw;
@@ -1132,6 +1133,29 @@ __global__ void k_fill(uint32_t *p, size_t words)
     }
 }
 } // namespace
+
+namespace {
+// rows x S bytes at dst, each a copy of the S bytes at src.
+__global__ void k_broadcast(uint8_t *dst, const uint8_t *src, size_t S, uint32_t rows)
+{
+    const size_t v16 = S / 16, total = v16 * rows;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+        d4[i] = s4[i % v16];
+}
+} // namespace
+
+cudaError_t launch_broadcast(uint8_t *dst, const uint8_t *src, size_t S, uint32_t rows, cudaStream_t s,
+                             uint64_t *launches)
+{
+    if (rows == 0) return cudaSuccess;
+    const size_t total = S / 16 * rows;
+    const unsigned blocks = (unsigned)std::min<size_t>((total + kThreads - 1) / kThreads, (size_t)kSms * 16);
+    k_broadcast<<<blocks, kThreads, 0, s>>>(dst, src, S, rows);
+    *launches += 1;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_fill(uint8_t *p, size_t bytes, cudaStream_t s)
 {

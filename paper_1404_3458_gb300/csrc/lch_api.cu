@@ -476,18 +476,46 @@ int encode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
     }
     int rc = ensure_tables(ctx, field, s);
     if (rc) return rc;
+    if (k == 1) { // F is the constant m_0: every parity row is a copy of row 0
+        CU(launch_broadcast(shards + S, shards, S, n - 1, s, &ctx->launches), "broadcast");
+        return LCH_OK;
+    }
     rc = ensure_scratch(ctx, (size_t)k * S);
     if (rc) return rc;
     uint8_t *mbar = ctx->scratch;
     // Algorithm 1 line 1: bar M_k = (Psi_k^0)^-1 [M_k]
     rc = transform(ctx, field, k, 0, 1, shards, mbar, S, s);
     if (rc) return rc;
-    // lines 2-4: bar F_i = Psi_k^{ik} [bar M_k] into rows ik .. ik+k-1
-    for (uint32_t i = 1; i < n / k; i++) {
-        rc = transform(ctx, field, k, i * k, 0, mbar, shards + (size_t)i * k * S, S, s);
-        if (rc) return rc;
-    }
-    return LCH_OK;
+    // lines 2-4: bar F_i = Psi_k^{ik} [bar M_k] into rows ik .. ik+k-1, all
+    // cosets at once: the levels of Psi_k with shift ik are levels 0..lg k-1 of
+    // an n-point transform with shift 0 on rows ik.., and every coset starts
+    // from bar M_k (source rows masked with k - 1).
+    const uint32_t lgk = lg2(k);
+    uint32_t a, b, lg[2];
+    pass_plan(ctx, field, lgk, S, &a, &b, lg);
+    const uint64_t cols = S / (field / 8);
+    auto coset_pass = [&](const uint8_t *src, uint32_t mask, uint32_t L0, uint32_t nlev, uint32_t lg_cw) -> int {
+        PassArgs p;
+        p.src = src;
+        p.dst = shards;
+        p.S = S;
+        p.h = n;
+        p.L0 = L0;
+        p.nlev = nlev;
+        p.l = 0;
+        p.inverse = 0;
+        p.rec = ctx->tab[field == LCH_GF16].rec;
+        p.lg_cw = lg_cw;
+        p.g0 = (k >> (L0 + nlev)) << L0; // first group on row k
+        p.ngroups = (n >> nlev) - p.g0;
+        p.src_mask = mask;
+        const uint64_t rows = n - k;
+        PROFM(LCH_KIND_PASS, 2 * rows * S, rows / 2 * cols * nlev, launch_pass(field, p, s, &ctx->launches));
+        return LCH_OK;
+    };
+    if (b == 0) return coset_pass(mbar, k - 1, 0, a, lg[0]);
+    if ((rc = coset_pass(mbar, k - 1, a, b, lg[1]))) return rc;
+    return coset_pass(shards, 0xFFFFFFFFu, 0, a, lg[0]);
 }
 
 // ---------------------------------------------------------------- batch planner

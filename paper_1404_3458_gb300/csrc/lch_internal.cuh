@@ -145,6 +145,13 @@ struct PassArgs {
     int inverse;      // 1: (Psi)^-1 order, 0: Psi order
     const uint8_t *rec;
     uint32_t lg_cw = 0; // log2 column-tile bytes (0: the default for nlev and S)
+    // Row groups [g0, g0 + ngroups) of the h >> nlev groups (ngroups 0: all
+    // from g0).  Rows are read from src at (row & src_mask): with src holding
+    // k rows and src_mask = k - 1 every k-row coset starts from the same rows
+    // (the coset transforms of Algorithm 1 in one launch).
+    uint32_t g0 = 0;
+    uint32_t ngroups = 0;
+    uint32_t src_mask = 0xFFFFFFFFu;
 };
 cudaError_t launch_pass(int r, const PassArgs &a, cudaStream_t s, uint64_t *launches);
 
@@ -286,6 +293,9 @@ uint32_t plan_deriv_lg_cw(int r, uint32_t nlev, int mode, size_t S, bool batch);
 uint32_t max_lg_cw(int r, uint32_t nlev, size_t S);
 // ... inside the batch kernel (whose shared memory is fixed).
 uint32_t batch_max_lg_cw(int r, uint32_t nlev);
+// rows x S bytes at dst, each row a copy of the S bytes at src.
+cudaError_t launch_broadcast(uint8_t *dst, const uint8_t *src, size_t S, uint32_t rows, cudaStream_t s,
+                             uint64_t *launches);
 // Fill `bytes` bytes with a fixed pseudo-random pattern (autotuning inputs).
 cudaError_t launch_fill(uint8_t *p, size_t bytes, cudaStream_t s);
 

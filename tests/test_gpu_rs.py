@@ -160,3 +160,19 @@ def test_shortened_encode_reuses_cached_locator():
                 assert np.array_equal(d.cpu().numpy(), gpu_encode(ctx2, r, n, k, h))
     finally:
         ctx2.close()
+
+
+@pytest.mark.parametrize("r,n,k,S", [(16, 65536, 1, 16), (16, 4096, 2, 48), (8, 256, 4, 32), (16, 65536, 16, 16),
+                                     (16, 65536, 1024, 32), (8, 256, 128, 16), (16, 8192, 512, 80)])
+def test_encode_many_cosets(ctx, r, n, k, S):
+    """Algorithm 1 with many parity cosets (all cosets run as one pass set;
+    k = 1 is a broadcast): sampled parity rows against the oracle, message
+    rows untouched."""
+    host = message(n, k, S, seed=9000 + n + k)
+    got = gpu_encode(ctx, r, n, k, host)
+    assert np.array_equal(got[:k], host[:k])
+    cols = elem_cols(S, r, 4, seed=k)
+    g = np.random.default_rng(n + k)
+    rows = np.unique(np.concatenate([[k, n - 1], k + g.choice(n - k, min(n - k, 40), replace=False)]))
+    expect = O.rs_encode(r, n, k, elems(host, r, cols), rows=rows)
+    assert np.array_equal(elems(got, r)[rows][:, cols], expect[rows])
