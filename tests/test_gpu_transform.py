@@ -71,3 +71,28 @@ def test_derivative_matches_oracle(ctx, r, lgh, S):
     got = elems(dev.cpu().numpy(), r)
     cols = elem_cols(S, r, 8, seed=lgh)
     assert np.array_equal(got[:, cols], O.derivative(r, elems(host, r, cols)))
+
+
+@pytest.mark.parametrize("lgh", list(range(8, 17)))
+def test_roundtrip_config2_sizes(ctx, lgh):
+    """lch_fft / lch_ifft round trips at h = 2^8 .. 2^16 in GF(2^16) with
+    64 KiB shards (4 KiB for h >= 2^15, which would otherwise need 2-4 GB):
+    every byte returns, and sampled transform values match direct evaluation."""
+    import torch
+
+    r, h = 16, 1 << lgh
+    S = 65536 if lgh <= 14 else 4096
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(4000 + lgh)
+    dev = torch.randint(0, 256, (h, S), dtype=torch.uint8, device="cuda", generator=gen)
+    orig = dev.clone()
+    cols = elem_cols(S, r, 4, seed=lgh)
+    byte_cols = np.concatenate([[2 * c, 2 * c + 1] for c in cols])
+    coef = orig[:, torch.from_numpy(byte_cols).cuda()].cpu().numpy()
+    ctx.fft(r, 0, dev)
+    rows = np.random.default_rng(lgh).choice(h, 16, replace=False)
+    got = dev[torch.from_numpy(rows).cuda()][:, torch.from_numpy(byte_cols).cuda()].cpu().numpy()
+    assert np.array_equal(O.to_elems(got, r), O.fft(r, 0, O.to_elems(coef, r), rows=rows))
+    ctx.ifft(r, 0, dev)
+    torch.cuda.synchronize()
+    assert torch.equal(dev, orig)

@@ -139,3 +139,33 @@ def test_tune_set_none_restores_defaults(tctx):
     tctx.fft(r, 0, b)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+def test_large_gf16_with_autotuned_plans(tctx):
+    """The measured workload (n = 65536, k = 32768, 4 KiB shards) under the
+    autotuned plans that bench.py uses: sampled parity rows against the
+    oracle, then a decode of 32768 random erasures restores every byte."""
+    import torch
+
+    w = WL.WORKLOADS["large_gf16"]
+    r, n, k, S = w.field, w.n, w.k, w.shard_bytes
+    for h in (k, n):
+        tctx.autotune(r, h, S)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(77)
+    dev = torch.zeros((n, S), dtype=torch.uint8, device="cuda")
+    dev[:k] = torch.randint(0, 256, (k, S), dtype=torch.uint8, device="cuda", generator=gen)
+    tctx.rs_encode(n, k, r, dev)
+    cw = dev.clone()
+    cols = elem_cols(S, r, 3, seed=5)
+    byte_cols = torch.from_numpy(np.concatenate([[2 * c, 2 * c + 1] for c in cols])).cuda()
+    rows = k + np.random.default_rng(6).choice(n - k, 12, replace=False)
+    msg = O.to_elems(dev[:, byte_cols].cpu().numpy(), r)
+    msg[k:] = 0
+    expect = O.rs_encode(r, n, k, msg, rows=rows)
+    assert np.array_equal(O.to_elems(dev[:, byte_cols].cpu().numpy(), r)[rows], expect[rows])
+    mask = WL.erasure_mask(n, n - k, w.seed + 100)
+    dev[torch.from_numpy(mask != 0).cuda()] = 0x5A
+    tctx.rs_decode(n, k, r, dev, mask)
+    torch.cuda.synchronize()
+    assert torch.equal(dev, cw)
