@@ -243,8 +243,7 @@ def run_ours(args):
         enc_ms.append(ev[3 * i].elapsed_time(ev[3 * i + 1]))
         dec_ms.append(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]))
 
-    # timed region: exactly K steps, profiling events on the launch stream
-    ctx.profile_enable(True)
+    # timed region: exactly K steps, nothing recorded between the launches
     launches0 = ctx.launches
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -259,6 +258,13 @@ def run_ours(args):
     launches = ctx.launches - launches0
     ms = start.elapsed_time(end)
     clk.summary_cache = clk.summary()
+    # per-kernel breakdown: the same K steps again with the library's CUDA
+    # events around every launch (events between launches keep consecutive
+    # kernels from overlapping, so this run is not the timed one)
+    ctx.profile_enable(True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
     kinds = {}
     for kind, name in enumerate(["pass", "deriv", "rowscale", "locator"]):
         kinds[name] = ctx.profile(kind)

@@ -325,7 +325,8 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, uint32_t lg_cw, uin
     const size_t col0 = (size_t)y0 << lg_cw;
     const uint32_t ntiles = col0 < a.S ? (uint32_t)((a.S - col0 + col_step - 1) / col_step) : 0;
 
-    stage_pass_recs<R>(a, nrows, hibase, sm); // first copy group
+    stage_pass_recs<R>(a, nrows, hibase, sm); // first copy group (static tables)
+    pdl_wait(); // the predecessor's writes are visible from here on
 
     auto issue = [&](uint32_t t, uint32_t *dstbuf) {
         const size_t col = col0 + (size_t)t * col_step;
@@ -377,6 +378,7 @@ template <int R, int INV>
 __global__ void __launch_bounds__(kPassThreads, 1) k_pass(PassArgs a, uint32_t lg_cw)
 {
     extern __shared__ __align__(128) uint8_t sm[];
+    pdl_trigger();
     pass_body<R, INV>(a, lg_cw, blockIdx.x, blockIdx.y, gridDim.y, sm);
 }
 
@@ -400,12 +402,13 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_p(PassArgs a, uint32_t
     if (i0 >= i1) return;
     const uint32_t g_first = i0 / ntiles + a.g0;
 
+    pdl_trigger();
     // tile of item k into dstbuf, with its group's records when k opens a group
     auto issue = [&](uint32_t k, uint8_t *dstbuf) {
         const uint32_t g = k / ntiles + a.g0, t = k - (k / ntiles) * ntiles;
         const uint32_t lo = g & ((1u << a.L0) - 1u);
         const uint32_t hibase = (g >> a.L0) << (a.L0 + nlev);
-        if (k == i0 || t == 0) stage_pass_recs<R>(a, nrows, hibase, sm + ((g - g_first) & 1u) * tab_sz);
+        if (k != i0 && t == 0) stage_pass_recs<R>(a, nrows, hibase, sm + ((g - g_first) & 1u) * tab_sz);
         const size_t col = (size_t)t << lg_cw;
         const size_t rem = a.S - col;
         const uint32_t width = rem < cw ? (uint32_t)rem : cw;
@@ -418,6 +421,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_p(PassArgs a, uint32_t
         }
     };
 
+    // the first group's records (static tables) before the predecessor is done
+    stage_pass_recs<R>(a, nrows, (g_first >> a.L0) << (a.L0 + nlev), sm);
+    pdl_wait(); // the predecessor's writes are visible from here on
     issue(i0, buf0);
     cp_async_commit();
     if (i0 + 1 < i1) issue(i0 + 1, buf0 + tile_bytes);
@@ -709,6 +715,7 @@ __device__ __forceinline__ void deriv_body(const DerivArgs &a, uint32_t lg_cw, u
         const uint8_t *src = (inv ? a.binvrec : a.brec) + row * FT<R>::rec_bytes + c * 16;
         cp_async16(sm + set * rec_bytes + rec_dst<R>(nrows, q, c), src);
     }
+    pdl_wait(); // the predecessor's writes are visible from here on
 
     auto issue = [&](uint32_t t, uint8_t *dstbuf) {
         const size_t col = col0 + (size_t)t * col_step;
@@ -749,6 +756,7 @@ template <int R, int MODE>
 __global__ void __launch_bounds__(kPassThreads, 1) k_deriv(DerivArgs a, uint32_t lg_cw)
 {
     extern __shared__ __align__(128) uint8_t sm[];
+    pdl_trigger();
     deriv_body<R, MODE>(a, lg_cw, blockIdx.x, blockIdx.y, gridDim.y, sm);
 }
 
@@ -780,6 +788,8 @@ __global__ void __launch_bounds__(kThreads)
 {
     __shared__ __align__(128) uint8_t T[kRowsPerCta * FT<R>::rec_bytes];
     __shared__ uint32_t ks[kRowsPerCta];
+    pdl_trigger();
+    pdl_wait(); // coef and src come from predecessors
     const uint32_t r0 = blockIdx.x * kRowsPerCta;
     constexpr uint32_t cpr = FT<R>::rec_bytes / 16;
     for (uint32_t v = threadIdx.x; v < kRowsPerCta * cpr; v += blockDim.x) {
@@ -864,8 +874,8 @@ cudaError_t pass_impl(const PassArgs &a, cudaStream_t s)
         if (items < (1ull << 32)) {
             const uint32_t ctas = (uint32_t)std::min<uint64_t>(items, kSms);
             const size_t smem = 2 * tab + (2 * (size_t)nrows << lg_cw);
-            k_pass_p<R, INV><<<ctas, kPassThreads, smem, s>>>(a, lg_cw, (uint32_t)ntiles_p, (uint32_t)items);
-            return cudaGetLastError();
+            return launch_pdl(k_pass_p<R, INV>, dim3(ctas), dim3(kPassThreads), smem, s, a, lg_cw, (uint32_t)ntiles_p,
+                              (uint32_t)items);
         }
     }
     lg_cw = a.lg_cw ? a.lg_cw : pick_lg_cw(nrows, a.S);
@@ -878,8 +888,7 @@ cudaError_t pass_impl(const PassArgs &a, cudaStream_t s)
     if (y > ntiles) y = ntiles;
     if (y < 1) y = 1;
     if (y > 65535) y = 65535;
-    k_pass<R, INV><<<dim3(ngroups, (unsigned)y, 1), kPassThreads, smem, s>>>(a, lg_cw);
-    return cudaGetLastError();
+    return launch_pdl(k_pass<R, INV>, dim3(ngroups, (unsigned)y, 1), dim3(kPassThreads), smem, s, a, lg_cw);
 }
 
 // ---------------------------------------------------------------- batches
@@ -1205,8 +1214,7 @@ cudaError_t deriv_impl(const DerivArgs &a, cudaStream_t s)
     if (y > ntiles) y = ntiles;
     if (y < 1) y = 1;
     if (y > 65535) y = 65535;
-    k_deriv<R, MODE><<<dim3(ngroups, (unsigned)y, 1), kPassThreads, smem, s>>>(a, lg_cw);
-    return cudaGetLastError();
+    return launch_pdl(k_deriv<R, MODE>, dim3(ngroups, (unsigned)y, 1), dim3(kPassThreads), smem, s, a, lg_cw);
 }
 
 cudaError_t launch_deriv(int r, int mode, const DerivArgs &a, cudaStream_t s, uint64_t *launches)
@@ -1221,10 +1229,12 @@ cudaError_t launch_rowscale(int r, uint8_t *dst, const uint8_t *src, size_t S, u
 {
     if (rows == 0) return cudaSuccess;
     const uint32_t ctas = (rows + kRowsPerCta - 1) / kRowsPerCta;
+    cudaError_t e;
     if (r == 8)
-        k_rowscale<8><<<ctas, kThreads, 0, s>>>(dst, src, S, rows, coef, skip_zero);
+        e = launch_pdl(k_rowscale<8>, dim3(ctas), dim3(kThreads), 0, s, dst, src, S, rows, coef, skip_zero);
     else
-        k_rowscale<16><<<ctas, kThreads, 0, s>>>(dst, src, S, rows, coef, skip_zero);
+        e = launch_pdl(k_rowscale<16>, dim3(ctas), dim3(kThreads), 0, s, dst, src, S, rows, coef, skip_zero);
+    if (e != cudaSuccess) return e;
     *launches += 1;
     return cudaGetLastError();
 }

@@ -119,6 +119,32 @@ struct FieldTables {
     uint32_t wbase[16] = {};  // W_i(w_{2^i}) (host copy, for tests/diagnostics)
 };
 
+// ------------------------------------------------ programmatic dependent launch
+// Kernels of the encode/decode chains are launched with programmatic stream
+// serialization: a kernel may start (and stage its static tables) while its
+// predecessor on the stream drains.  Each such kernel calls pdl_wait() before
+// it reads or writes memory a predecessor may touch; both calls are no-ops
+// for a normal launch.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ----------------------------------------------------------------- launches
 // Every launcher returns the CUDA error of its launch and adds the number of
 // kernels it launched to *launches.
