@@ -291,6 +291,8 @@ def run_ours(args):
                 "peak": round(alu_peak, 2), "unit": "Gmul/s", "frac": round(achieved_mul / alu_peak, 4),
                 "peak_source": (f"derived: 152 SMs x 64 ALU lanes/clk x {sm_mhz:.0f} MHz / 8.5 ALU ops per "
                                 "GF(2^16) split-table multiply-add"),
+                "alu_pipe": {"peak_tops": round(152 * 64 * sm_mhz * 1e6 / 1e12, 2), "ops_per_mult": 8.5,
+                             "achieved_tops": round(achieved_mul * 8.5 / 1e3, 2)},
                 "traffic": KPASS_TRAFFIC["bytes"], "traffic_alg_bytes": KPASS_TRAFFIC["alg_bytes"],
                 "traffic_launch": KPASS_TRAFFIC["launch"], "launches_per_step": d["launches"] / args.steps,
                 "share_of_kernel_time": round(d["ms"] / tot_ms, 4) if tot_ms else None,

@@ -234,18 +234,6 @@ __host__ __device__ __forceinline__ uint32_t tab_bytes(uint32_t nrec)
     return (nrec * FT<R>::rec_bytes + 127u) & ~127u;
 }
 
-// Copy record q (global layout: the rec_bytes of one record back to back)
-// into the region layout above, 16 bytes per thread step.
-template <int R>
-__device__ __forceinline__ void stage_chunk(uint8_t *tab, uint32_t nrec, uint32_t q, uint32_t c, const uint4 *src)
-{
-    uint32_t dst;
-    if constexpr (R == 16)
-        dst = c < 8 ? (q << 7) + (c << 4) : (c < 16 ? ((nrec + q) << 7) + ((c - 8) << 4) : (nrec << 8) + (q << 5) + ((c - 16) << 4));
-    else
-        dst = (q << 8) + (c << 4);
-    *reinterpret_cast<uint4 *>(tab + dst) = src[c];
-}
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
@@ -908,8 +896,8 @@ __device__ __forceinline__ void rows_body(const BatchOp &op, uint32_t r0, uint32
                 for (size_t v = threadIdx.x; v < S / 16; v += blockDim.x) d4[v] = make_uint4(0, 0, 0, 0);
             continue;
         }
-        for (uint32_t idx = threadIdx.x; idx < FT<R>::rec_entries; idx += blockDim.x)
-            rec_store<R>(sm, idx, rec_entry<R>(c, idx));
+        for (uint32_t ch = threadIdx.x; ch < FT<R>::rec_bytes / 16; ch += blockDim.x)
+            reinterpret_cast<uint4 *>(sm)[ch] = rec_chunk<R>(c, ch);
         __syncthreads();
         const uint4 *s4 = reinterpret_cast<const uint4 *>(op.src + (size_t)row * S);
         for (size_t v = threadIdx.x; v < S / 16; v += blockDim.x) {
