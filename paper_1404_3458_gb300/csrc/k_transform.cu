@@ -371,11 +371,13 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(PassArgs a, uint32_t l
 }
 
 // Persistent form: one CTA per SM takes a contiguous range of the
-// (row group, column tile) items in group-major order.  Two record buffers
-// and two tile buffers: the records of the next group and the tile after
-// next are copied in while the current tile is transformed.  Needs at least
-// two tiles per group (then at most two groups are live at a time).
-template <int R, int INV>
+// (row group, column tile) items in group-major order, with two tile buffers
+// (the tile after next is copied in while the current one is transformed).
+// RB = 2: two record buffers, the next group's records are copied in ahead
+// (needs at least two tiles per group, so that at most two groups are live);
+// RB = 1: one record buffer, refilled when the CTA reaches a new group (a
+// short stall once per group, but room for wider tiles).
+template <int R, int INV, int RB>
 __global__ void __launch_bounds__(kPassThreads, 1) k_pass_p(PassArgs a, uint32_t lg_cw, uint32_t ntiles, uint32_t items)
 {
     extern __shared__ __align__(128) uint8_t sm[];
@@ -383,20 +385,21 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_p(PassArgs a, uint32_t
     const uint32_t tab_sz = tab_bytes<R>(nrec);
     const uint32_t stab0 = (uint32_t)__cvta_generic_to_shared(sm);
     const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
-    uint8_t *const buf0 = sm + 2 * tab_sz;
+    uint8_t *const buf0 = sm + RB * tab_sz;
     const uint32_t tile_bytes = nrows << lg_cw;
     const uint32_t i0 = (uint32_t)((uint64_t)blockIdx.x * items / gridDim.x);
     const uint32_t i1 = (uint32_t)((uint64_t)(blockIdx.x + 1) * items / gridDim.x);
     if (i0 >= i1) return;
     const uint32_t g_first = i0 / ntiles + a.g0;
+    auto rec_buf = [&](uint32_t g) -> uint32_t { return RB == 2 ? ((g - g_first) & 1u) * tab_sz : 0u; };
 
     pdl_trigger();
-    // tile of item k into dstbuf, with its group's records when k opens a group
+    // tile of item k into dstbuf (RB = 2: with its group's records when k opens a group)
     auto issue = [&](uint32_t k, uint8_t *dstbuf) {
         const uint32_t g = k / ntiles + a.g0, t = k - (k / ntiles) * ntiles;
         const uint32_t lo = g & ((1u << a.L0) - 1u);
         const uint32_t hibase = (g >> a.L0) << (a.L0 + nlev);
-        if (k != i0 && t == 0) stage_pass_recs<R>(a, nrows, hibase, sm + ((g - g_first) & 1u) * tab_sz);
+        if (RB == 2 && k != i0 && t == 0) stage_pass_recs<R>(a, nrows, hibase, sm + rec_buf(g));
         const size_t col = (size_t)t << lg_cw;
         const size_t rem = a.S - col;
         const uint32_t width = rem < cw ? (uint32_t)rem : cw;
@@ -421,9 +424,17 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_p(PassArgs a, uint32_t
         uint8_t *data = buf0 + ((k - i0) & 1u) * tile_bytes;
         const uint32_t sdata = (uint32_t)__cvta_generic_to_shared(data);
         const uint32_t g = k / ntiles + a.g0, t = k - (k / ntiles) * ntiles;
-        cp_async_wait1(); // item k's tile and records have landed for this thread
+        if (RB == 1 && k != i0 && t == 0) {
+            // new group: refill the record buffer (the previous item is done
+            // with it) and wait for it together with the tiles in flight
+            stage_pass_recs<R>(a, nrows, (g >> a.L0) << (a.L0 + nlev), sm);
+            cp_async_commit();
+            cp_async_wait_all();
+        } else {
+            cp_async_wait1(); // item k's tile and records have landed for this thread
+        }
         __syncthreads();
-        pass_tile<R, INV>(sdata, stab0 + ((g - g_first) & 1u) * tab_sz, nlev, lg_w);
+        pass_tile<R, INV>(sdata, stab0 + rec_buf(g), nlev, lg_w);
         __syncthreads();
         {
             const uint32_t lo = g & ((1u << a.L0) - 1u);
@@ -854,21 +865,19 @@ cudaError_t pass_impl(const PassArgs &a, cudaStream_t s)
     uint32_t lg_cw = a.lg_cw ? a.lg_cw : pick_lg_cw(nrows, a.S);
     const size_t tab = tab_bytes<R>(nrows - 1);
     const uint32_t ngroups = a.ngroups ? a.ngroups : (a.h >> a.nlev) - a.g0;
-    // persistent form: two record sets, at least two tiles per group
-    while (lg_cw > 4 && 2 * tab + (2 * (size_t)nrows << lg_cw) > kPassSmem) lg_cw--;
-    const size_t ntiles_p = (a.S + (1ull << lg_cw) - 1) >> lg_cw;
-    if (ntiles_p >= 2 && 2 * tab + (2 * (size_t)nrows << lg_cw) <= kPassSmem) {
-        const uint64_t items = (uint64_t)ngroups * ntiles_p;
-        if (items < (1ull << 32)) {
-            const uint32_t ctas = (uint32_t)std::min<uint64_t>(items, kSms);
-            const size_t smem = 2 * tab + (2 * (size_t)nrows << lg_cw);
-            return launch_pdl(k_pass_p<R, INV>, dim3(ctas), dim3(kPassThreads), smem, s, a, lg_cw, (uint32_t)ntiles_p,
-                              (uint32_t)items);
-        }
-    }
-    lg_cw = a.lg_cw ? a.lg_cw : pick_lg_cw(nrows, a.S);
-    const size_t smem = tab + (2 * (size_t)nrows << lg_cw);
+    while (lg_cw > 4 && tab + (2 * (size_t)nrows << lg_cw) > kPassSmem) lg_cw--;
+    const size_t tiles = 2 * (size_t)nrows << lg_cw;
     const size_t ntiles = (a.S + (1ull << lg_cw) - 1) >> lg_cw;
+    const uint64_t items = (uint64_t)ngroups * ntiles;
+    if (ntiles >= 2 && items < (1ull << 32)) {
+        // persistent form: two record sets when they fit beside the tiles
+        const uint32_t ctas = (uint32_t)std::min<uint64_t>(items, kSms);
+        if (2 * tab + tiles <= kPassSmem)
+            return launch_pdl(k_pass_p<R, INV, 2>, dim3(ctas), dim3(kPassThreads), 2 * tab + tiles, s, a, lg_cw,
+                              (uint32_t)ntiles, (uint32_t)items);
+        return launch_pdl(k_pass_p<R, INV, 1>, dim3(ctas), dim3(kPassThreads), tab + tiles, s, a, lg_cw,
+                          (uint32_t)ntiles, (uint32_t)items);
+    }
     // About 4 tiles per CTA and at least ~6 CTAs per SM in total.
     size_t y = (ntiles + 3) / 4;
     const size_t want = (kSms * 6 + ngroups - 1) / ngroups;
@@ -876,7 +885,7 @@ cudaError_t pass_impl(const PassArgs &a, cudaStream_t s)
     if (y > ntiles) y = ntiles;
     if (y < 1) y = 1;
     if (y > 65535) y = 65535;
-    return launch_pdl(k_pass<R, INV>, dim3(ngroups, (unsigned)y, 1), dim3(kPassThreads), smem, s, a, lg_cw);
+    return launch_pdl(k_pass<R, INV>, dim3(ngroups, (unsigned)y, 1), dim3(kPassThreads), tab + tiles, s, a, lg_cw);
 }
 
 // ---------------------------------------------------------------- batches
@@ -1078,10 +1087,14 @@ cudaError_t configure_transform_kernels()
     if ((e = cudaFuncSetAttribute(k_pass<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_pass<16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_pass<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_p<8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_p<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_p<16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_p<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<8, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<8, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<16, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<16, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<8, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<8, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<16, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<16, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv<8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
@@ -1103,10 +1116,9 @@ uint32_t plan_deriv_lg_cw(int r, uint32_t nlev, int mode, size_t S, bool batch)
 
 uint32_t max_lg_cw(int r, uint32_t nlev, size_t S)
 {
-    // the persistent pass keeps two record sets
     const size_t tab = r == 16 ? tab_bytes<16>((1u << nlev) - 1) : tab_bytes<8>((1u << nlev) - 1);
     uint32_t lg = 4;
-    while (lg < 12 && 2 * tab + (2ull << nlev << (lg + 1)) <= kPassSmem && (1ull << (lg + 1)) < 2 * S) lg++;
+    while (lg < 12 && tab + (2ull << nlev << (lg + 1)) <= kPassSmem && (1ull << (lg + 1)) < 2 * S) lg++;
     return lg;
 }
 
