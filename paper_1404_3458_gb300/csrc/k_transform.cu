@@ -196,9 +196,20 @@ __device__ __forceinline__ void round_levels(uint32_t *x, uint32_t tab, uint32_t
 
 // One round: every thread takes 2^Q rows (bits s0 .. s0+Q-1 free) of one
 // column word, runs Q levels in registers and writes the rows back.
-template <int R, int INV, int Q>
+// Where the last round of a tile writes its rows in global memory: tile row m
+// is row hibase | (m << L0) | lo, columns [col, col + width).
+struct TileOut {
+    uint8_t *dst;
+    size_t S;
+    size_t col;
+    uint32_t L0, hibase, lo, width;
+};
+
+// GST = true: the round writes its results to global memory (the tile's last
+// round) instead of back to the tile.
+template <int R, int INV, int Q, bool GST>
 __device__ __forceinline__ void round_q(uint32_t data, uint32_t tab, uint32_t nrec, uint32_t nrows, uint32_t lg_w,
-                                        uint32_t s0)
+                                        uint32_t s0, const TileOut &o)
 {
     const uint32_t W = 1u << lg_w;
     const uint32_t items = (nrows >> Q) << lg_w;
@@ -211,20 +222,29 @@ __device__ __forceinline__ void round_q(uint32_t data, uint32_t tab, uint32_t nr
 #pragma unroll
         for (int u = 0; u < (1 << Q); u++) x[u] = lds_u32(p + u * stride);
         round_levels<R, INV, Q, 0>(x, tab, nrec, nrows, base, s0);
+        if constexpr (GST) {
+            if (w * 4 < o.width) {
+                uint8_t *q = o.dst + (size_t)(o.hibase | (base << o.L0) | o.lo) * o.S + o.col + w * 4;
+                const size_t rstep = o.S << (s0 + o.L0);
 #pragma unroll
-        for (int u = 0; u < (1 << Q); u++) sts_u32(p + u * stride, x[u]);
+                for (int u = 0; u < (1 << Q); u++) *reinterpret_cast<uint32_t *>(q + u * rstep) = x[u];
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < (1 << Q); u++) sts_u32(p + u * stride, x[u]);
+        }
     }
 }
 
-template <int R, int INV>
+template <int R, int INV, bool GST = false>
 __device__ __forceinline__ void run_round(uint32_t q, uint32_t data, uint32_t tab, uint32_t nrec, uint32_t nrows,
-                                          uint32_t lg_w, uint32_t s0)
+                                          uint32_t lg_w, uint32_t s0, const TileOut &o = TileOut{})
 {
     switch (q) {
-    case 1: round_q<R, INV, 1>(data, tab, nrec, nrows, lg_w, s0); break;
-    case 2: round_q<R, INV, 2>(data, tab, nrec, nrows, lg_w, s0); break;
-    case 3: round_q<R, INV, 3>(data, tab, nrec, nrows, lg_w, s0); break;
-    default: round_q<R, INV, 4>(data, tab, nrec, nrows, lg_w, s0); break;
+    case 1: round_q<R, INV, 1, GST>(data, tab, nrec, nrows, lg_w, s0, o); break;
+    case 2: round_q<R, INV, 2, GST>(data, tab, nrec, nrows, lg_w, s0, o); break;
+    case 3: round_q<R, INV, 3, GST>(data, tab, nrec, nrows, lg_w, s0, o); break;
+    default: round_q<R, INV, 4, GST>(data, tab, nrec, nrows, lg_w, s0, o); break;
     }
 }
 
@@ -233,7 +253,6 @@ __host__ __device__ __forceinline__ uint32_t tab_bytes(uint32_t nrec)
 {
     return (nrec * FT<R>::rec_bytes + 127u) & ~127u;
 }
-
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
@@ -273,24 +292,27 @@ __device__ __forceinline__ void stage_pass_recs(const PassArgs &a, uint32_t nrow
     }
 }
 
-// The levels of one tile in shared memory: register rounds of <= 4 levels.
+// The levels of one tile in shared memory: register rounds of <= 4 levels;
+// the last round writes the tile's rows to global memory (o).
 template <int R, int INV>
-__device__ __forceinline__ void pass_tile(uint32_t sdata, uint32_t stab, uint32_t nlev, uint32_t lg_w)
+__device__ __forceinline__ void pass_tile(uint32_t sdata, uint32_t stab, uint32_t nlev, uint32_t lg_w, const TileOut &o)
 {
     const uint32_t nrows = 1u << nlev, nrec = nrows - 1;
     const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, qb = nlev - qa;
     if (INV) {
-        run_round<R, INV>(qa, sdata, stab, nrec, nrows, lg_w, 0);
         if (qb) {
+            run_round<R, INV>(qa, sdata, stab, nrec, nrows, lg_w, 0);
             __syncthreads();
-            run_round<R, INV>(qb, sdata, stab, nrec, nrows, lg_w, qa);
+            run_round<R, INV, true>(qb, sdata, stab, nrec, nrows, lg_w, qa, o);
+        } else {
+            run_round<R, INV, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, o);
         }
     } else {
         if (qb) {
             run_round<R, INV>(qb, sdata, stab, nrec, nrows, lg_w, qa);
             __syncthreads();
         }
-        run_round<R, INV>(qa, sdata, stab, nrec, nrows, lg_w, 0);
+        run_round<R, INV, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, o);
     }
 }
 
@@ -339,20 +361,11 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, uint32_t lg_cw, uin
         const uint32_t sdata = (uint32_t)__cvta_generic_to_shared(data);
         cp_async_wait1(); // tile t (and the records) have landed for this thread
         __syncthreads();
-        pass_tile<R, INV>(sdata, stab, nlev, lg_w);
-        __syncthreads();
         {
             const size_t col = col0 + (size_t)t * col_step;
             const size_t rem = a.S - col;
-            const uint32_t width = rem < cw ? (uint32_t)rem : cw;
-            for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
-                const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
-                if (c * 16 < width) {
-                    const size_t row = hibase | ((size_t)m << a.L0) | lo;
-                    *reinterpret_cast<uint4 *>(a.dst + row * a.S + col + c * 16) =
-                        reinterpret_cast<const uint4 *>(data)[v];
-                }
-            }
+            const TileOut o{a.dst, a.S, col, a.L0, hibase, lo, rem < cw ? (uint32_t)rem : cw};
+            pass_tile<R, INV>(sdata, stab, nlev, lg_w, o);
         }
         __syncthreads(); // everyone has read this buffer
         if (t + 2 < ntiles) issue(t + 2, data);
@@ -434,22 +447,13 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_p(PassArgs a, uint32_t
             cp_async_wait1(); // item k's tile and records have landed for this thread
         }
         __syncthreads();
-        pass_tile<R, INV>(sdata, stab0 + rec_buf(g), nlev, lg_w);
-        __syncthreads();
         {
             const uint32_t lo = g & ((1u << a.L0) - 1u);
             const uint32_t hibase = (g >> a.L0) << (a.L0 + nlev);
             const size_t col = (size_t)t << lg_cw;
             const size_t rem = a.S - col;
-            const uint32_t width = rem < cw ? (uint32_t)rem : cw;
-            for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
-                const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
-                if (c * 16 < width) {
-                    const size_t row = hibase | ((size_t)m << a.L0) | lo;
-                    *reinterpret_cast<uint4 *>(a.dst + row * a.S + col + c * 16) =
-                        reinterpret_cast<const uint4 *>(data)[v];
-                }
-            }
+            const TileOut o{a.dst, a.S, col, a.L0, hibase, lo, rem < cw ? (uint32_t)rem : cw};
+            pass_tile<R, INV>(sdata, stab0 + rec_buf(g), nlev, lg_w, o);
         }
         __syncthreads(); // everyone has read this tile and this group's records
         if (k + 2 < i1) issue(k + 2, data);
