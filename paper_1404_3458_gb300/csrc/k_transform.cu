@@ -688,6 +688,26 @@ __host__ __device__ __forceinline__ uint32_t deriv_rec_bytes(uint32_t nrows, int
     return (mode == 2 ? 2u : 1u) * tab_bytes<R>(nrows);
 }
 
+// Records of B and/or B^-1 for the rows of the group (hibase, lo), copied
+// with cp.async into the region layout (the caller commits).
+template <int R, int MODE>
+__device__ __forceinline__ void stage_deriv_recs(const DerivArgs &a, uint32_t nrows, uint32_t hibase, uint32_t lo,
+                                                 uint8_t *sm)
+{
+    constexpr bool kMulB = MODE != 1, kInv = MODE != 0;
+    constexpr uint32_t kSets = (kMulB ? 1 : 0) + (kInv ? 1 : 0);
+    const uint32_t rec_bytes = tab_bytes<R>(nrows);
+    constexpr uint32_t cpr = FT<R>::rec_bytes / 16;
+    for (uint32_t v = threadIdx.x; v < nrows * cpr * kSets; v += blockDim.x) {
+        const uint32_t set = v / (nrows * cpr), vv = v - set * nrows * cpr;
+        const uint32_t q = vv / cpr, c = vv - q * cpr;
+        const size_t row = hibase | ((size_t)q << a.L0) | lo;
+        const bool inv = !kMulB || set == 1;
+        const uint8_t *src = (inv ? a.binvrec : a.brec) + row * FT<R>::rec_bytes + c * 16;
+        cp_async16(sm + set * rec_bytes + rec_dst<R>(nrows, q, c), src);
+    }
+}
+
 template <int R, int MODE>
 __device__ __forceinline__ void deriv_body(const DerivArgs &a, uint32_t lg_cw, uint32_t g, uint32_t y0, uint32_t ystep,
                                            uint8_t *sm)
@@ -708,16 +728,7 @@ __device__ __forceinline__ void deriv_body(const DerivArgs &a, uint32_t lg_cw, u
     const size_t col0 = (size_t)y0 << lg_cw;
     const uint32_t ntiles = col0 < a.S ? (uint32_t)((a.S - col0 + col_step - 1) / col_step) : 0;
 
-    // Records of B and/or B^-1 for the tile rows.
-    constexpr uint32_t cpr = FT<R>::rec_bytes / 16;
-    for (uint32_t v = threadIdx.x; v < nrows * cpr * kSets; v += blockDim.x) {
-        const uint32_t set = v / (nrows * cpr), vv = v - set * nrows * cpr;
-        const uint32_t q = vv / cpr, c = vv - q * cpr;
-        const size_t row = hibase | ((size_t)q << a.L0) | lo;
-        const bool inv = !kMulB || set == 1;
-        const uint8_t *src = (inv ? a.binvrec : a.brec) + row * FT<R>::rec_bytes + c * 16;
-        cp_async16(sm + set * rec_bytes + rec_dst<R>(nrows, q, c), src);
-    }
+    stage_deriv_recs<R, MODE>(a, nrows, hibase, lo, sm);
     pdl_wait(); // the predecessor's writes are visible from here on
 
     auto issue = [&](uint32_t t, uint8_t *dstbuf) {
@@ -761,6 +772,82 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_deriv(DerivArgs a, uint32_t
     extern __shared__ __align__(128) uint8_t sm[];
     pdl_trigger();
     deriv_body<R, MODE>(a, lg_cw, blockIdx.x, blockIdx.y, gridDim.y, sm);
+}
+
+// Persistent form (as k_pass_p with one record buffer): one CTA per SM walks a
+// contiguous range of (row group, column tile) items in group-major order,
+// refilling its per-row records when it reaches a new group; two stages of
+// (u tile, accumulator tile) double-buffer the loads.
+template <int R, int MODE>
+__global__ void __launch_bounds__(kPassThreads, 1) k_deriv_p(DerivArgs a, uint32_t lg_cw, uint32_t ntiles, uint32_t items)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
+    constexpr bool kX = MODE == 1, kMulB = MODE != 1;
+    const uint32_t nlev = a.nlev, nrows = 1u << nlev;
+    const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
+    const uint32_t rec_bytes = tab_bytes<R>(nrows);
+    const uint32_t s_b = (uint32_t)__cvta_generic_to_shared(sm);
+    const uint32_t s_binv = s_b + (kMulB ? rec_bytes : 0);
+    uint8_t *stage0 = sm + deriv_rec_bytes<R>(nrows, MODE);
+    const uint32_t tile_bytes = nrows << lg_cw;
+    const uint32_t stage_bytes = 2 * tile_bytes; // u tile + accumulator tile
+    const uint32_t i0 = (uint32_t)((uint64_t)blockIdx.x * items / gridDim.x);
+    const uint32_t i1 = (uint32_t)((uint64_t)(blockIdx.x + 1) * items / gridDim.x);
+    if (i0 >= i1) return;
+    pdl_trigger();
+    auto group = [&](uint32_t k, uint32_t &hibase, uint32_t &lo, uint32_t &t) {
+        const uint32_t g = k / ntiles;
+        t = k - g * ntiles;
+        lo = g & ((1u << a.L0) - 1u);
+        hibase = (g >> a.L0) << (a.L0 + nlev);
+    };
+    auto issue = [&](uint32_t k, uint8_t *dstbuf) {
+        uint32_t hibase, lo, t;
+        group(k, hibase, lo, t);
+        const size_t col = (size_t)t << lg_cw;
+        const size_t rem = a.S - col;
+        const uint32_t width = rem < cw ? (uint32_t)rem : cw;
+        for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
+            const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
+            if (c * 16 < width) {
+                const size_t off = (hibase | ((size_t)m << a.L0) | lo) * a.S + col + c * 16;
+                cp_async16(dstbuf + v * 16, a.src + off);
+                if (kX) cp_async16(dstbuf + tile_bytes + v * 16, a.xin + off);
+            }
+        }
+    };
+    {
+        uint32_t hibase, lo, t;
+        group(i0, hibase, lo, t);
+        stage_deriv_recs<R, MODE>(a, nrows, hibase, lo, sm); // static tables
+    }
+    pdl_wait(); // the predecessor's writes are visible from here on
+    issue(i0, stage0);
+    cp_async_commit();
+    if (i0 + 1 < i1) issue(i0 + 1, stage0 + stage_bytes);
+    cp_async_commit();
+    for (uint32_t k = i0; k < i1; k++) {
+        uint8_t *stage = stage0 + ((k - i0) & 1u) * stage_bytes;
+        const uint32_t su = (uint32_t)__cvta_generic_to_shared(stage), sacc = su + tile_bytes;
+        uint32_t hibase, lo, t;
+        group(k, hibase, lo, t);
+        if (k != i0 && t == 0) {
+            // new group: refill the records (the previous item is done with them)
+            stage_deriv_recs<R, MODE>(a, nrows, hibase, lo, sm);
+            cp_async_commit();
+            cp_async_wait_all();
+        } else {
+            cp_async_wait1();
+        }
+        __syncthreads();
+        const size_t col = (size_t)t << lg_cw;
+        const size_t rem = a.S - col;
+        deriv_tile<R, MODE>(a, su, sacc, s_b, s_binv, lg_w, hibase, lo, col, rem < cw ? (uint32_t)rem : cw);
+        __syncthreads();
+        if (k + 2 < i1) issue(k + 2, stage);
+        cp_async_commit();
+    }
+    cp_async_wait_all();
 }
 
 // Per-row scaling dst[row] = coef[row] (.) src[row] for kRowsPerCta rows per
@@ -1091,6 +1178,12 @@ cudaError_t configure_transform_kernels()
     if ((e = cudaFuncSetAttribute(k_pass<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_pass<16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_pass<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_deriv_p<8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_deriv_p<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_deriv_p<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_deriv_p<16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_deriv_p<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_deriv_p<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_pass_p<8, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_pass_p<8, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_pass_p<16, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
@@ -1211,6 +1304,12 @@ cudaError_t deriv_impl(const DerivArgs &a, cudaStream_t s)
     const uint32_t lg_cw = deriv_lg_cw<R>(a.nlev, MODE, a.S, kPassSmem);
     const size_t smem = deriv_rec_bytes<R>(nrows, MODE) + 2 * 2 * ((size_t)nrows << lg_cw);
     const uint32_t ngroups = a.h >> a.nlev;
+    const size_t ntiles_p = (a.S + (1ull << lg_cw) - 1) >> lg_cw;
+    if (ntiles_p >= 2 && (uint64_t)ngroups * ntiles_p < (1ull << 32)) {
+        const uint32_t items = (uint32_t)(ngroups * ntiles_p);
+        return launch_pdl(k_deriv_p<R, MODE>, dim3(std::min<uint32_t>(items, kSms)), dim3(kPassThreads), smem, s, a,
+                          lg_cw, (uint32_t)ntiles_p, items);
+    }
     const size_t ntiles = (a.S + (1ull << lg_cw) - 1) >> lg_cw;
     size_t y = (ntiles + 7) / 8;
     const size_t want = (kSms * 6 + ngroups - 1) / ngroups;
