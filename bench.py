@@ -65,7 +65,7 @@ def parse():
     p.add_argument("--no-tune", action="store_true", help="keep the default pass plans (no lch_autotune)")
     p.add_argument("--tune-cache", default=None, help="JSON cache of tuned pass plans (read, and written if new)")
     p.add_argument("--no-serve", action="store_true")
-    p.add_argument("--serve-requests", type=int, default=256)
+    p.add_argument("--serve-requests", type=int, default=1024)
     return p.parse_args()
 
 
@@ -472,7 +472,7 @@ def run_serving(ctx, torch, args, rank):
     budget = 40 * 10**9
     out = {"budget_bytes": budget, "requests_per_rate": N,
            "workload": "Poisson arrivals, 70% encode / 30% decode, (n,k,field,S,erasures) as in the batched mix"}
-    for rate in (1e3, 1e4, 1e5):
+    for rate in (1e3, 1e4, 3e4, 1e5):
         arr = SV.poisson_arrivals(rate, N, WL.SEED_BASE + int(rate) + rank)
         res = {}
         for name in ("served", "plain"):

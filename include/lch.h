@@ -268,8 +268,8 @@ typedef struct lch_tuning {
 /* Time candidate plans for (field, h, shard_bytes) on `stream` and keep the
  * fastest on the context; *best receives it.  Candidates: the splits with
  * both passes <= 8 levels among {ceil(lg h/2), floor(lg h/2), lg h-8, 8}, and
- * for each pass the default tile width and its two neighbours that fit in
- * shared memory.  Each pass is timed with CUDA events, forward and inverse,
+ * for each pass the default tile width, one narrower and two wider ones that
+ * fit in shared memory.  Each pass is timed with CUDA events, forward and inverse,
  * after one warm-up, on h * shard_bytes bytes of context scratch filled with a
  * fixed pattern (grown by cudaMalloc if needed; no caller data is touched).
  * Synchronises `stream`.  Errors: LCH_EINVAL (bad field, h not a power of two

@@ -313,13 +313,14 @@ int time_pass(lch_ctx *ctx, int field, uint32_t h, uint8_t *buf, size_t S, uint3
     return LCH_OK;
 }
 
-// Fastest tile width for one pass among the default and its neighbours.
+// Fastest tile width for one pass among the default, one narrower and two
+// wider (as far as shared memory allows).
 int tune_pass(lch_ctx *ctx, int field, uint32_t h, uint8_t *buf, size_t S, uint32_t L0, uint32_t nlev, EventPair &ev,
               cudaStream_t s, uint32_t *best_lg, float *best_ms)
 {
     const uint32_t def = plan_lg_cw(1u << nlev, S), hi = max_lg_cw(field, nlev, S);
     *best_ms = -1.f;
-    for (uint32_t lg = def > 4 ? def - 1 : 4; lg <= def + 1 && lg <= hi; lg++) {
+    for (uint32_t lg = def > 4 ? def - 1 : 4; lg <= def + 2 && lg <= hi; lg++) {
         float ms = 0;
         int rc = time_pass(ctx, field, h, buf, S, L0, nlev, lg, ev, s, &ms);
         if (rc) return rc;

@@ -119,7 +119,7 @@ class _Inflight:
 
 class Server:
     def __init__(self, ctx: "lch.Context", budget_bytes: int, max_inflight: int = 3, max_batch: int = 1024,
-                 min_batch: int = 16, max_direct: int = 32):
+                 min_batch: int = 16, max_direct: int = 32, prefer_batch: bool = False):
         import torch
 
         self.torch = torch
@@ -130,6 +130,7 @@ class Server:
         self.max_batch = max_batch
         self.min_batch = min_batch
         self.max_direct = max_direct
+        self.prefer_batch = prefer_batch  # a backlog of min_batch goes to a free slot before the direct stream
         self.streams = [torch.cuda.Stream() for _ in range(max_inflight)]
         # A lone request skips batch planning and runs as a single-codeword
         # call; each launch slot has its own context so those calls never
@@ -233,7 +234,8 @@ class Server:
                 self._release(r)
                 blocked = False
             # launch waiting requests one by one while the direct stream has room
-            while waiting and len(direct) < self.max_direct and not blocked:
+            while (waiting and len(direct) < self.max_direct and not blocked
+                   and not (self.prefer_batch and len(waiting) >= self.min_batch and free_slots)):
                 r = waiting[0]
                 if _estimate(r) > self.arena.size - self.arena.used or not self._admit(r):
                     if not inflight and not direct and _estimate(r) > self.arena.size:
