@@ -26,7 +26,7 @@
  *   - error locator: Pi(j) = prod_{y in E, y != j} (j + y) by direct product
  *     (Appendix, eq. Pi'(j)2).
  *
- * Readings of the paper (all listed in the design doc):
+ * Readings of the paper where it leaves a choice open:
  *   - the basis v_0..v_{r-1} is the polynomial basis, v_j = x^j, so the field
  *     element w_i has the bit pattern of i and w_a + w_b = w_{a xor b};
  *   - GF(2^8) reduces by x^8+x^4+x^3+x^2+1 (0x11D), GF(2^16) by
