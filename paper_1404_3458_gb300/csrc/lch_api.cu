@@ -521,7 +521,7 @@ int encode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
 
 // ---------------------------------------------------------------- batch planner
 
-constexpr size_t kTaskBytes = 512 * 1024; // target data per task
+constexpr size_t kTaskBytes = 8u << 20; // target data per task (measured: 8 MB beats 128 KB..2 MB)
 
 struct PlanTask {
     uint32_t stage, op, cw, g0, g1;
