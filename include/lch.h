@@ -285,6 +285,10 @@ LCH_API int lch_autotune(lch_ctx *ctx, int field, uint32_t h, size_t shard_bytes
  * that should use them. */
 LCH_API int lch_tune_set(lch_ctx *ctx, int field, uint32_t h, size_t shard_bytes, const lch_tuning *plan);
 
+/* The plan installed on ctx for (field, h, shard_bytes) (ms is set to 0),
+ * e.g. to give other contexts the same plans; LCH_EINVAL when there is none. */
+LCH_API int lch_tune_get(lch_ctx *ctx, int field, uint32_t h, size_t shard_bytes, lch_tuning *plan);
+
 #ifdef __cplusplus
 }
 #endif

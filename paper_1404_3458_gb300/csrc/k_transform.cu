@@ -391,22 +391,19 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(PassArgs a, uint32_t l
 // RB = 1: one record buffer, refilled when the CTA reaches a new group (a
 // short stall once per group, but room for wider tiles).
 template <int R, int INV, int RB>
-__global__ void __launch_bounds__(kPassThreads, 1) k_pass_p(PassArgs a, uint32_t lg_cw, uint32_t ntiles, uint32_t items)
+__device__ __forceinline__ void pass_items(const PassArgs &a, uint32_t lg_cw, uint32_t ntiles, uint32_t i0, uint32_t i1,
+                                           uint8_t *sm)
 {
-    extern __shared__ __align__(128) uint8_t sm[];
     const uint32_t nlev = a.nlev, nrows = 1u << nlev, nrec = nrows - 1;
     const uint32_t tab_sz = tab_bytes<R>(nrec);
     const uint32_t stab0 = (uint32_t)__cvta_generic_to_shared(sm);
     const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
     uint8_t *const buf0 = sm + RB * tab_sz;
     const uint32_t tile_bytes = nrows << lg_cw;
-    const uint32_t i0 = (uint32_t)((uint64_t)blockIdx.x * items / gridDim.x);
-    const uint32_t i1 = (uint32_t)((uint64_t)(blockIdx.x + 1) * items / gridDim.x);
     if (i0 >= i1) return;
     const uint32_t g_first = i0 / ntiles + a.g0;
     auto rec_buf = [&](uint32_t g) -> uint32_t { return RB == 2 ? ((g - g_first) & 1u) * tab_sz : 0u; };
 
-    pdl_trigger();
     // tile of item k into dstbuf (RB = 2: with its group's records when k opens a group)
     auto issue = [&](uint32_t k, uint8_t *dstbuf) {
         const uint32_t g = k / ntiles + a.g0, t = k - (k / ntiles) * ntiles;
@@ -460,6 +457,17 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_p(PassArgs a, uint32_t
         cp_async_commit();
     }
     cp_async_wait_all();
+    __syncthreads();
+}
+
+template <int R, int INV, int RB>
+__global__ void __launch_bounds__(kPassThreads, 1) k_pass_p(PassArgs a, uint32_t lg_cw, uint32_t ntiles, uint32_t items)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
+    const uint32_t i0 = (uint32_t)((uint64_t)blockIdx.x * items / gridDim.x);
+    const uint32_t i1 = (uint32_t)((uint64_t)(blockIdx.x + 1) * items / gridDim.x);
+    pdl_trigger();
+    pass_items<R, INV, RB>(a, lg_cw, ntiles, i0, i1, sm);
 }
 
 __global__ void __launch_bounds__(kThreads) k_superset(SupersetArgs a, uint32_t lg_cw)
@@ -779,9 +787,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_deriv(DerivArgs a, uint32_t
 // refilling its per-row records when it reaches a new group; two stages of
 // (u tile, accumulator tile) double-buffer the loads.
 template <int R, int MODE>
-__global__ void __launch_bounds__(kPassThreads, 1) k_deriv_p(DerivArgs a, uint32_t lg_cw, uint32_t ntiles, uint32_t items)
+__device__ __forceinline__ void deriv_items(const DerivArgs &a, uint32_t lg_cw, uint32_t ntiles, uint32_t i0, uint32_t i1,
+                                            uint8_t *sm)
 {
-    extern __shared__ __align__(128) uint8_t sm[];
     constexpr bool kX = MODE == 1, kMulB = MODE != 1;
     const uint32_t nlev = a.nlev, nrows = 1u << nlev;
     const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
@@ -791,10 +799,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_deriv_p(DerivArgs a, uint32
     uint8_t *stage0 = sm + deriv_rec_bytes<R>(nrows, MODE);
     const uint32_t tile_bytes = nrows << lg_cw;
     const uint32_t stage_bytes = 2 * tile_bytes; // u tile + accumulator tile
-    const uint32_t i0 = (uint32_t)((uint64_t)blockIdx.x * items / gridDim.x);
-    const uint32_t i1 = (uint32_t)((uint64_t)(blockIdx.x + 1) * items / gridDim.x);
     if (i0 >= i1) return;
-    pdl_trigger();
     auto group = [&](uint32_t k, uint32_t &hibase, uint32_t &lo, uint32_t &t) {
         const uint32_t g = k / ntiles;
         t = k - g * ntiles;
@@ -848,6 +853,17 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_deriv_p(DerivArgs a, uint32
         cp_async_commit();
     }
     cp_async_wait_all();
+    __syncthreads();
+}
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(kPassThreads, 1) k_deriv_p(DerivArgs a, uint32_t lg_cw, uint32_t ntiles, uint32_t items)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
+    const uint32_t i0 = (uint32_t)((uint64_t)blockIdx.x * items / gridDim.x);
+    const uint32_t i1 = (uint32_t)((uint64_t)(blockIdx.x + 1) * items / gridDim.x);
+    pdl_trigger();
+    deriv_items<R, MODE>(a, lg_cw, ntiles, i0, i1, sm);
 }
 
 // Per-row scaling dst[row] = coef[row] (.) src[row] for kRowsPerCta rows per
@@ -1081,7 +1097,7 @@ __device__ __forceinline__ uint64_t global_ns()
 
 // Shared memory of a batch task body (the largest: a derivative pass with
 // 2 x 256 GF(2^16) records and 2 stages of 2 tiles; tiles are narrowed to fit).
-__host__ __device__ constexpr size_t batch_body_smem() { return 192 * 1024; }
+__host__ __device__ constexpr size_t batch_body_smem() { return 212 * 1024; }
 
 // The persistent batch kernel: one CTA per SM pulls tasks in queue order.
 __global__ void __launch_bounds__(kPassThreads, 1)

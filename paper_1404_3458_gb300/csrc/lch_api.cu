@@ -521,7 +521,18 @@ int encode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
 
 // ---------------------------------------------------------------- batch planner
 
-constexpr size_t kTaskBytes = 8u << 20; // target data per task (measured: 8 MB beats 128 KB..2 MB)
+// Target data per task: about 8 tasks per CTA over the whole batch, between
+// 256 KB and 8 MB.  Large batches take large tasks (fewer task switches: 8 MB
+// was 2-3 % faster than 512 KB on 4096 codewords); small batches take small
+// ones, so that a single large codeword's stage still spreads over the SMs
+// (with 8 MB tasks a 32-codeword batch ran 3-5x slower than plain calls).
+size_t batch_task_bytes(const lch_codeword *cws, uint32_t count)
+{
+    uint64_t total = 0;
+    for (uint32_t c = 0; c < count; c++) total += (uint64_t)cws[c].n * cws[c].shard_bytes;
+    const uint64_t want = total / (8ull * 152);
+    return (size_t)std::min<uint64_t>(8ull << 20, std::max<uint64_t>(256ull << 10, want));
+}
 
 struct PlanTask {
     uint32_t stage, op, cw, g0, g1;
@@ -538,6 +549,7 @@ struct Planner {
     std::vector<PlanTask> tasks;
     std::vector<uint32_t> masks; // packed erasure bitmaps
     size_t scratch = 0;          // bytes reserved so far
+    size_t task_bytes = 512 * 1024; // target data per task (batch_task_bytes)
 
     uint8_t *reserve(size_t bytes)
     {
@@ -551,9 +563,16 @@ struct Planner {
         return (uint32_t)ops.size() - 1;
     }
     // Split an op over `units` rows or row groups of `unit_bytes` each.
+    // Tasks of a pass or derivative op over `groups` row groups of
+    // group_bytes each (a task is a range of whole row groups; splitting
+    // large groups by column tiles was measured and did not pay).
+    void add_group_tasks(uint32_t stage, BatchOp op, uint32_t cw, uint32_t groups, size_t group_bytes, size_t)
+    {
+        add_tasks(stage, add_op(op), cw, groups, group_bytes);
+    }
     void add_tasks(uint32_t stage, uint32_t op, uint32_t cw, uint32_t units, size_t unit_bytes)
     {
-        const uint32_t per = (uint32_t)std::max<size_t>(1, kTaskBytes / std::max<size_t>(1, unit_bytes));
+        const uint32_t per = (uint32_t)std::max<size_t>(1, task_bytes / std::max<size_t>(1, unit_bytes));
         for (uint32_t g = 0; g < units; g += per) {
             const uint32_t g1 = std::min(units, g + per);
             tasks.push_back({stage, op, cw, g, g1, (uint64_t)(g1 - g) * unit_bytes});
@@ -587,7 +606,7 @@ struct Planner {
             op.nlev = nl[p];
             op.l = l;
             op.tab0 = ctx->tab[field == LCH_GF16].rec;
-            add_tasks(stage + p, add_op(op), cw, h >> nl[p], ((size_t)1 << nl[p]) * S);
+            add_group_tasks(stage + p, op, cw, h >> nl[p], ((size_t)1 << nl[p]) * S, S);
         }
         return stage + (b ? 2 : 1);
     }
@@ -650,7 +669,7 @@ void plan_decode(Planner &P, uint32_t cw, uint32_t n, int field, uint8_t *shards
         d.L0 = 0;
         d.nlev = a;
         d.lg_cw = plan_deriv_lg_cw(field, a, 2, S, true);
-        P.add_tasks(stage++, P.add_op(d), cw, n >> a, ((size_t)1 << a) * S);
+        P.add_group_tasks(stage++, d, cw, n >> a, ((size_t)1 << a) * S, S);
     } else {
         d.mode = 0;
         d.dst = phi2;
@@ -658,13 +677,13 @@ void plan_decode(Planner &P, uint32_t cw, uint32_t n, int field, uint8_t *shards
         d.L0 = 0;
         d.nlev = a;
         d.lg_cw = plan_deriv_lg_cw(field, a, 0, S, true);
-        P.add_tasks(stage++, P.add_op(d), cw, n >> a, ((size_t)1 << a) * S);
+        P.add_group_tasks(stage++, d, cw, n >> a, ((size_t)1 << a) * S, S);
         d.mode = 1;
         d.aux = phi2;
         d.L0 = a;
         d.nlev = b;
         d.lg_cw = plan_deriv_lg_cw(field, b, 1, S, true);
-        P.add_tasks(stage++, P.add_op(d), cw, n >> b, ((size_t)1 << b) * S);
+        P.add_group_tasks(stage++, d, cw, n >> b, ((size_t)1 << b) * S, S);
     }
     stage = P.add_transform(stage, cw, field, n, 0, 0, phi2, phi2, S);
     rows.src = phi2;
@@ -800,6 +819,7 @@ int batch_create(lch_ctx *ctx, int op, const lch_codeword *cws, uint32_t count, 
         }
     }
     Planner sizing{ctx};
+    sizing.task_bytes = batch_task_bytes(cws, count);
     plan_batch(sizing, op, cws, count);
     const BatchLayout L = batch_layout(sizing, count);
     lch_batch *b = new (std::nothrow) lch_batch;
@@ -824,6 +844,7 @@ int batch_create(lch_ctx *ctx, int op, const lch_codeword *cws, uint32_t count, 
     b->counters = mem + L.counters;
     b->counter_bytes = L.total - L.counters;
     Planner P{ctx, b->scratch, b->masks};
+    P.task_bytes = sizing.task_bytes;
     plan_batch(P, op, cws, count);
     // stage-major queue, largest tasks first within a stage
     std::stable_sort(P.tasks.begin(), P.tasks.end(), [](const PlanTask &x, const PlanTask &y) {
@@ -1040,6 +1061,7 @@ LCH_API int lch_batch_bytes(lch_ctx *ctx, int op, const lch_codeword *cws, uint3
     int rc;
     if ((rc = validate_batch(op, cws, count))) return rc;
     Planner sizing{ctx};
+    sizing.task_bytes = batch_task_bytes(cws, count);
     plan_batch(sizing, op, cws, count);
     *bytes = batch_layout(sizing, count).total;
     return LCH_OK;
@@ -1228,6 +1250,20 @@ LCH_API int lch_autotune(lch_ctx *ctx, int field, uint32_t h, size_t shard_bytes
     if (rc) return rc;
     ctx->tuned[std::make_tuple(field, lgh, shard_bytes)] = lch_ctx::Plan{out.split, {out.lg_tile_low, out.lg_tile_high}};
     *best = out;
+    return LCH_OK;
+}
+
+LCH_API int lch_tune_get(lch_ctx *ctx, int field, uint32_t h, size_t shard_bytes, lch_tuning *plan)
+{
+    int rc;
+    if ((rc = check_field(field)) || (rc = check_len("h", h, field))) return rc;
+    if (!ctx || !plan) return fail(LCH_EINVAL, "NULL argument");
+    const auto it = ctx->tuned.find(std::make_tuple(field, lg2(h), shard_bytes));
+    if (it == ctx->tuned.end()) return fail(LCH_EINVAL, "no plan installed for this (field, h, shard_bytes)");
+    plan->split = it->second.a;
+    plan->lg_tile_low = it->second.lg[0];
+    plan->lg_tile_high = it->second.lg[1];
+    plan->ms = 0.f;
     return LCH_OK;
 }
 

@@ -94,6 +94,7 @@ def load() -> ctypes.CDLL:
         "lch_batch_set_wait_limit": (i, [vp, u32]),
         "lch_batch_selftest_stall": (i, [vp, vp]),
         "lch_tune_set": (i, [vp, i, u32, sz, ctypes.POINTER(Tuning)]),
+        "lch_tune_get": (i, [vp, i, u32, sz, ctypes.POINTER(Tuning)]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -273,6 +274,14 @@ class Context:
             return
         t = Tuning(int(plan["split"]), int(plan["lg_tile_low"]), int(plan["lg_tile_high"]), float(plan.get("ms", 0.0)))
         _check(load().lch_tune_set(self._h, field, h, shard_bytes, ctypes.byref(t)))
+
+    def tune_get(self, field: int, h: int, shard_bytes: int):
+        """lch_tune_get: the plan installed for (field, h, shard_bytes) as a
+        dict, or None when there is none."""
+        t = Tuning()
+        if load().lch_tune_get(self._h, field, h, shard_bytes, ctypes.byref(t)) != LCH_OK:
+            return None
+        return t.as_dict()
 
     # Sec. III: Psi_h^l and its inverse, in place on h rows.
     def fft(self, field: int, l: int, buf, stream=None):

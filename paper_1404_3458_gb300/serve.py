@@ -144,9 +144,19 @@ class Server:
         """Build, before serving, what each context builds on first use for
         these (field, n, k, shard_bytes) shapes: field tables, FWHT(log)
         tables, shortened-code locators and scratch of the largest size (a
-        first use synchronises the device, which would stall the loop)."""
+        first use synchronises the device, which would stall the loop).  Pass
+        plans installed on the server's main context are copied to the
+        contexts of the direct calls and of the launch slots."""
         torch = self.torch
         seen = sorted(set(shapes), key=lambda t: t[1] * t[3], reverse=True)
+        for field, n, k, S in seen:
+            for h in {n, k}:
+                if h < 2 or h & (h - 1):
+                    continue
+                plan = self.ctx.tune_get(field, h, S)
+                if plan is not None:
+                    for c in [self.direct_ctx] + self.slot_ctx:
+                        c.tune_set(field, h, S, plan)
         for field, n, k, S in seen:
             buf = torch.zeros((n, S), dtype=torch.uint8, device="cuda")
             mask = np.zeros(n, dtype=np.uint8)
@@ -275,9 +285,14 @@ class Server:
                     still.append(f)
             inflight = still
             # admit whatever fits and launch it as one batch per operation
-            # (fewer than min_batch also go out as a batch once no more arrive
-            # and the direct stream is full)
-            enough = len(waiting) >= self.min_batch or (waiting and not pending and len(direct) >= self.max_direct)
+            # a backlog goes out as a batch once the direct stream is full (or,
+            # with prefer_batch, as soon as min_batch requests wait); fewer
+            # than min_batch also go once no more requests arrive
+            full = len(direct) >= self.max_direct
+            if self.prefer_batch:
+                enough = len(waiting) >= self.min_batch or (waiting and not pending and full)
+            else:
+                enough = full and (len(waiting) >= self.min_batch or (waiting and not pending))
             if enough and free_slots and not blocked:
                 slot = free_slots[-1]
                 stream = self.streams[slot]
