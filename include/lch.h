@@ -219,6 +219,22 @@ LCH_API uint32_t lch_batch_tasks(const lch_batch *batch);
 
 LCH_API void lch_batch_destroy(lch_batch *batch);
 
+/* ---- Row packing (the paper has no counterpart) ----------------------------
+ * Utilities for callers that hold only some rows of a codeword, e.g. the
+ * surviving shards before rs_decode or the recovered ones after it: they move
+ * whole rows between a codeword buffer and a packed buffer of consecutive
+ * rows.  idx is a DEVICE array of `count` uint32 row indices; src and dst are
+ * device buffers of shard_bytes-byte rows (16-byte aligned, shard_bytes a
+ * nonzero multiple of 16).  Indices are not checked against the buffers; they
+ * must be in range, and for a scatter distinct.  Enqueued on `stream`; count 0
+ * is a no-op.  No context needed.
+ *   gather:  dst row i      = src row idx[i]
+ *   scatter: dst row idx[i] = src row i */
+LCH_API int lch_rows_gather(const void *src, void *dst, const uint32_t *idx, uint32_t count, size_t shard_bytes,
+                            void *stream);
+LCH_API int lch_rows_scatter(const void *src, void *dst, const uint32_t *idx, uint32_t count, size_t shard_bytes,
+                             void *stream);
+
 /* Static text for a status code. */
 LCH_API const char *lch_strerror(int status);
 

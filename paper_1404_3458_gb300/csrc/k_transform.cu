@@ -1279,6 +1279,35 @@ cudaError_t launch_broadcast(uint8_t *dst, const uint8_t *src, size_t S, uint32_
     return cudaGetLastError();
 }
 
+namespace {
+// GATHER: dst row i = src row idx[i]; else (scatter) dst row idx[i] = src row i.
+template <bool GATHER>
+__global__ void k_rows_move(uint8_t *__restrict__ dst, const uint8_t *__restrict__ src, const uint32_t *__restrict__ idx,
+                            uint32_t count, size_t S)
+{
+    const size_t v16 = S / 16, total = v16 * count;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = i / v16, c = i - r * v16;
+        const size_t j = idx[r];
+        const size_t from = GATHER ? j : r, to = GATHER ? r : j;
+        reinterpret_cast<uint4 *>(dst + to * S)[c] = reinterpret_cast<const uint4 *>(src + from * S)[c];
+    }
+}
+} // namespace
+
+cudaError_t launch_rows_move(bool gather, uint8_t *dst, const uint8_t *src, const uint32_t *idx, uint32_t count,
+                             size_t S, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    const size_t total = S / 16 * count;
+    const unsigned blocks = (unsigned)std::min<size_t>((total + kThreads - 1) / kThreads, (size_t)kSms * 16);
+    if (gather)
+        k_rows_move<true><<<blocks, kThreads, 0, s>>>(dst, src, idx, count, S);
+    else
+        k_rows_move<false><<<blocks, kThreads, 0, s>>>(dst, src, idx, count, S);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fill(uint8_t *p, size_t bytes, cudaStream_t s)
 {
     k_fill<<<kSms * 4, kThreads, 0, s>>>(reinterpret_cast<uint32_t *>(p), bytes / 4);

@@ -1156,6 +1156,34 @@ LCH_API void lch_batch_destroy(lch_batch *b)
     batch_free(b);
 }
 
+namespace {
+int rows_move(bool gather, const void *src, void *dst, const uint32_t *idx, uint32_t count, size_t shard_bytes,
+              void *stream)
+{
+    if (count == 0) return LCH_OK;
+    if (!src || !dst || !idx) return fail(LCH_EINVAL, "NULL pointer");
+    if (((uintptr_t)src | (uintptr_t)dst) & 15u) return fail(LCH_EINVAL, "buffers must be 16-byte aligned");
+    if (shard_bytes == 0 || (shard_bytes & 15u))
+        return fail(LCH_EINVAL, "shard_bytes must be a nonzero multiple of 16, got %zu", shard_bytes);
+    CU(launch_rows_move(gather, static_cast<uint8_t *>(dst), static_cast<const uint8_t *>(src), idx, count,
+                        shard_bytes, (cudaStream_t)stream),
+       "row move");
+    return LCH_OK;
+}
+} // namespace
+
+LCH_API int lch_rows_gather(const void *src, void *dst, const uint32_t *idx, uint32_t count, size_t shard_bytes,
+                            void *stream)
+{
+    return rows_move(true, src, dst, idx, count, shard_bytes, stream);
+}
+
+LCH_API int lch_rows_scatter(const void *src, void *dst, const uint32_t *idx, uint32_t count, size_t shard_bytes,
+                             void *stream)
+{
+    return rows_move(false, src, dst, idx, count, shard_bytes, stream);
+}
+
 LCH_API const char *lch_strerror(int status)
 {
     switch (status) {

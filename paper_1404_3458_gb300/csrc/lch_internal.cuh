@@ -322,6 +322,9 @@ uint32_t batch_max_lg_cw(int r, uint32_t nlev);
 // rows x S bytes at dst, each row a copy of the S bytes at src.
 cudaError_t launch_broadcast(uint8_t *dst, const uint8_t *src, size_t S, uint32_t rows, cudaStream_t s,
                              uint64_t *launches);
+// Row gather (dst row i = src row idx[i]) or scatter (dst row idx[i] = src row i).
+cudaError_t launch_rows_move(bool gather, uint8_t *dst, const uint8_t *src, const uint32_t *idx, uint32_t count,
+                             size_t S, cudaStream_t s);
 // Fill `bytes` bytes with a fixed pseudo-random pattern (autotuning inputs).
 cudaError_t launch_fill(uint8_t *p, size_t bytes, cudaStream_t s);
 

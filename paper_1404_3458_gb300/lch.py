@@ -92,6 +92,8 @@ def load() -> ctypes.CDLL:
                                  ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
         "lch_autotune": (i, [vp, i, u32, sz, vp, ctypes.POINTER(Tuning)]),
         "lch_batch_set_wait_limit": (i, [vp, u32]),
+        "lch_rows_gather": (i, [vp, vp, vp, u32, sz, vp]),
+        "lch_rows_scatter": (i, [vp, vp, vp, u32, sz, vp]),
         "lch_batch_selftest_stall": (i, [vp, vp]),
         "lch_tune_set": (i, [vp, i, u32, sz, ctypes.POINTER(Tuning)]),
         "lch_tune_get": (i, [vp, i, u32, sz, ctypes.POINTER(Tuning)]),
@@ -139,6 +141,38 @@ def derivative_noalloc(field: int, buf, stream=None):
     (for callers that cannot call cudaMalloc).  h * shard_bytes <= 16 MiB."""
     p, S = _buf(buf)
     _check(load().lch_derivative_noalloc(field, buf.shape[0], p, S, _stream_handle(stream)))
+
+
+def _rows_args(src, dst, idx):
+    import torch
+
+    for t in (src, dst):
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.uint8 or t.dim() != 2 \
+                or not t.is_contiguous():
+            raise TypeError("expected contiguous CUDA uint8 tensors [rows, shard_bytes]")
+    if src.shape[1] != dst.shape[1]:
+        raise ValueError("src and dst must have the same shard_bytes")
+    if not isinstance(idx, torch.Tensor) or idx.device.type != "cuda" or idx.dtype != torch.int32 or idx.dim() != 1 \
+            or not idx.is_contiguous():
+        raise TypeError("expected a contiguous CUDA int32 index tensor")
+    return ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()), ctypes.c_void_p(idx.data_ptr()), \
+        idx.numel(), src.shape[1]
+
+
+def rows_gather(src, dst, idx, stream=None):
+    """lch_rows_gather: dst[i] = src[idx[i]] (rows); idx a CUDA int32 tensor."""
+    ps, pd, pi, cnt, S = _rows_args(src, dst, idx)
+    if dst.shape[0] < cnt:
+        raise ValueError("dst has fewer rows than idx")
+    _check(load().lch_rows_gather(ps, pd, pi, cnt, S, _stream_handle(stream)))
+
+
+def rows_scatter(src, dst, idx, stream=None):
+    """lch_rows_scatter: dst[idx[i]] = src[i] (rows); idx a CUDA int32 tensor."""
+    ps, pd, pi, cnt, S = _rows_args(src, dst, idx)
+    if src.shape[0] < cnt:
+        raise ValueError("src has fewer rows than idx")
+    _check(load().lch_rows_scatter(ps, pd, pi, cnt, S, _stream_handle(stream)))
 
 
 def _codeword_array(codewords, keep):

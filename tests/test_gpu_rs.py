@@ -176,3 +176,29 @@ def test_encode_many_cosets(ctx, r, n, k, S):
     rows = np.unique(np.concatenate([[k, n - 1], k + g.choice(n - k, min(n - k, 40), replace=False)]))
     expect = O.rs_encode(r, n, k, elems(host, r, cols), rows=rows)
     assert np.array_equal(elems(got, r)[rows][:, cols], expect[rows])
+
+
+def test_rows_gather_scatter_round_trip():
+    """lch_rows_scatter / lch_rows_gather move whole rows by a device index
+    array: scattering the survivors of a codeword into a fresh buffer and
+    decoding restores it; gathering the erased rows returns exactly them."""
+    import torch
+
+    r, n, k, S = 16, 256, 128, 208
+    host = message(n, k, S, seed=4242)
+    cw = gpu_encode(lch.Context(0), r, n, k, host)
+    mask = WL.erasure_mask(n, n - k, seed=17)
+    surv = np.nonzero(mask == 0)[0].astype(np.int32)
+    eras = np.nonzero(mask)[0].astype(np.int32)
+    packed = to_dev(cw[surv])
+    dev = torch.full((n, S), 0x77, dtype=torch.uint8, device="cuda")
+    lch.rows_scatter(packed, dev, torch.from_numpy(surv).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(dev.cpu().numpy()[surv], cw[surv])
+    c = lch.Context(0)
+    c.rs_decode(n, k, r, dev, mask)
+    out = torch.empty((eras.size, S), dtype=torch.uint8, device="cuda")
+    lch.rows_gather(dev, out, torch.from_numpy(eras).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), cw[eras])
+    c.close()
