@@ -158,7 +158,11 @@ template <> __device__ __forceinline__ uint4 rec_chunk<8>(uint32_t k, uint32_t c
 // Butterflies of local level j (0 <= j < Q) on the 2^Q registers x[], whose
 // row u is tile row base | (u << s0).  The pair (u, u + 2^j) belongs to block
 // (base >> (s0+j+1)) + (u >> (j+1)) of level s0 + j.
-template <int R, int INV, int Q, int J, int U>
+// ZT ("zero top"): the round holds the transform's top levels and l = 0, so
+// the pair (U, U + 2^J) has block start 0 and factor hatW(w_0) = 0 exactly
+// when U < 2^J (Sec. III.D: a shift of 0 saves h - 1 multiplications); those
+// butterflies reduce to b <- b + a.
+template <int R, int INV, int Q, int J, int U, bool ZT>
 struct LevelStep {
     static __device__ __forceinline__ void run(uint32_t *x, const TabRef<R> &t)
     {
@@ -167,7 +171,9 @@ struct LevelStep {
                 constexpr uint32_t K = (uint32_t)(U >> (J + 1));
                 uint32_t &A = x[U];
                 uint32_t &B = x[U | (1 << J)];
-                if constexpr (INV) {
+                if constexpr (ZT && U < (1 << J)) {
+                    B ^= A;
+                } else if constexpr (INV) {
                     B ^= A;
                     A ^= MulK<R, K>::f(B, t);
                 } else {
@@ -175,12 +181,12 @@ struct LevelStep {
                     B ^= A;
                 }
             }
-            LevelStep<R, INV, Q, J, U + 1>::run(x, t);
+            LevelStep<R, INV, Q, J, U + 1, ZT>::run(x, t);
         }
     }
 };
 
-template <int R, int INV, int Q, int JJ>
+template <int R, int INV, int Q, int JJ, bool ZT>
 __device__ __forceinline__ void round_levels(uint32_t *x, uint32_t tab, uint32_t nrec, uint32_t nrows,
                                              uint32_t base, uint32_t s0)
 {
@@ -189,8 +195,8 @@ __device__ __forceinline__ void round_levels(uint32_t *x, uint32_t tab, uint32_t
         const uint32_t s = s0 + J;
         const uint32_t q = rec_base(nrows, s) + (base >> (s + 1));
         const TabRef<R> t = tab_ref<R>(tab, q, nrec);
-        LevelStep<R, INV, Q, J, 0>::run(x, t);
-        round_levels<R, INV, Q, JJ + 1>(x, tab, nrec, nrows, base, s0);
+        LevelStep<R, INV, Q, J, 0, ZT>::run(x, t);
+        round_levels<R, INV, Q, JJ + 1, ZT>(x, tab, nrec, nrows, base, s0);
     }
 }
 
@@ -207,7 +213,7 @@ struct TileOut {
 
 // GST = true: the round writes its results to global memory (the tile's last
 // round) instead of back to the tile.
-template <int R, int INV, int Q, bool GST>
+template <int R, int INV, int Q, bool GST, bool ZT>
 __device__ __forceinline__ void round_q(uint32_t data, uint32_t tab, uint32_t nrec, uint32_t nrows, uint32_t lg_w,
                                         uint32_t s0, const TileOut &o)
 {
@@ -221,7 +227,7 @@ __device__ __forceinline__ void round_q(uint32_t data, uint32_t tab, uint32_t nr
         uint32_t x[1 << Q];
 #pragma unroll
         for (int u = 0; u < (1 << Q); u++) x[u] = lds_u32(p + u * stride);
-        round_levels<R, INV, Q, 0>(x, tab, nrec, nrows, base, s0);
+        round_levels<R, INV, Q, 0, ZT>(x, tab, nrec, nrows, base, s0);
         if constexpr (GST) {
             if (w * 4 < o.width) {
                 uint8_t *q = o.dst + (size_t)(o.hibase | (base << o.L0) | o.lo) * o.S + o.col + w * 4;
@@ -236,15 +242,15 @@ __device__ __forceinline__ void round_q(uint32_t data, uint32_t tab, uint32_t nr
     }
 }
 
-template <int R, int INV, bool GST = false>
+template <int R, int INV, bool GST = false, bool ZT = false>
 __device__ __forceinline__ void run_round(uint32_t q, uint32_t data, uint32_t tab, uint32_t nrec, uint32_t nrows,
                                           uint32_t lg_w, uint32_t s0, const TileOut &o = TileOut{})
 {
     switch (q) {
-    case 1: round_q<R, INV, 1, GST>(data, tab, nrec, nrows, lg_w, s0, o); break;
-    case 2: round_q<R, INV, 2, GST>(data, tab, nrec, nrows, lg_w, s0, o); break;
-    case 3: round_q<R, INV, 3, GST>(data, tab, nrec, nrows, lg_w, s0, o); break;
-    default: round_q<R, INV, 4, GST>(data, tab, nrec, nrows, lg_w, s0, o); break;
+    case 1: round_q<R, INV, 1, GST, ZT>(data, tab, nrec, nrows, lg_w, s0, o); break;
+    case 2: round_q<R, INV, 2, GST, ZT>(data, tab, nrec, nrows, lg_w, s0, o); break;
+    case 3: round_q<R, INV, 3, GST, ZT>(data, tab, nrec, nrows, lg_w, s0, o); break;
+    default: round_q<R, INV, 4, GST, ZT>(data, tab, nrec, nrows, lg_w, s0, o); break;
     }
 }
 
@@ -293,9 +299,12 @@ __device__ __forceinline__ void stage_pass_recs(const PassArgs &a, uint32_t nrow
 }
 
 // The levels of one tile in shared memory: register rounds of <= 4 levels;
-// the last round writes the tile's rows to global memory (o).
+// the last round writes the tile's rows to global memory (o).  zt: the tile
+// holds the transform's top levels with shift 0 (see LevelStep), which the
+// round over the tile's top levels uses.
 template <int R, int INV>
-__device__ __forceinline__ void pass_tile(uint32_t sdata, uint32_t stab, uint32_t nlev, uint32_t lg_w, const TileOut &o)
+__device__ __forceinline__ void pass_tile(uint32_t sdata, uint32_t stab, uint32_t nlev, uint32_t lg_w, const TileOut &o,
+                                          bool zt)
 {
     const uint32_t nrows = 1u << nlev, nrec = nrows - 1;
     const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, qb = nlev - qa;
@@ -303,17 +312,35 @@ __device__ __forceinline__ void pass_tile(uint32_t sdata, uint32_t stab, uint32_
         if (qb) {
             run_round<R, INV>(qa, sdata, stab, nrec, nrows, lg_w, 0);
             __syncthreads();
-            run_round<R, INV, true>(qb, sdata, stab, nrec, nrows, lg_w, qa, o);
+            if (zt)
+                run_round<R, INV, true, true>(qb, sdata, stab, nrec, nrows, lg_w, qa, o);
+            else
+                run_round<R, INV, true>(qb, sdata, stab, nrec, nrows, lg_w, qa, o);
+        } else if (zt) {
+            run_round<R, INV, true, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, o);
         } else {
             run_round<R, INV, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, o);
         }
     } else {
         if (qb) {
-            run_round<R, INV>(qb, sdata, stab, nrec, nrows, lg_w, qa);
+            if (zt)
+                run_round<R, INV, false, true>(qb, sdata, stab, nrec, nrows, lg_w, qa);
+            else
+                run_round<R, INV>(qb, sdata, stab, nrec, nrows, lg_w, qa);
             __syncthreads();
+            run_round<R, INV, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, o);
+        } else if (zt) {
+            run_round<R, INV, true, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, o);
+        } else {
+            run_round<R, INV, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, o);
         }
-        run_round<R, INV, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, o);
     }
+}
+
+// Whether a pass's tiles hold the transform's top levels with shift 0.
+__device__ __forceinline__ bool zero_top(const PassArgs &a)
+{
+    return a.l == 0 && a.g0 == 0 && (1u << (a.L0 + a.nlev)) == a.h;
 }
 
 // One CTA walks the column tiles [y0, y0 + ystep, ...) of row group g: the
@@ -365,7 +392,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, uint32_t lg_cw, uin
             const size_t col = col0 + (size_t)t * col_step;
             const size_t rem = a.S - col;
             const TileOut o{a.dst, a.S, col, a.L0, hibase, lo, rem < cw ? (uint32_t)rem : cw};
-            pass_tile<R, INV>(sdata, stab, nlev, lg_w, o);
+            pass_tile<R, INV>(sdata, stab, nlev, lg_w, o, zero_top(a));
         }
         __syncthreads(); // everyone has read this buffer
         if (t + 2 < ntiles) issue(t + 2, data);
@@ -450,7 +477,7 @@ __device__ __forceinline__ void pass_items(const PassArgs &a, uint32_t lg_cw, ui
             const size_t col = (size_t)t << lg_cw;
             const size_t rem = a.S - col;
             const TileOut o{a.dst, a.S, col, a.L0, hibase, lo, rem < cw ? (uint32_t)rem : cw};
-            pass_tile<R, INV>(sdata, stab0 + rec_buf(g), nlev, lg_w, o);
+            pass_tile<R, INV>(sdata, stab0 + rec_buf(g), nlev, lg_w, o, zero_top(a));
         }
         __syncthreads(); // everyone has read this tile and this group's records
         if (k + 2 < i1) issue(k + 2, data);

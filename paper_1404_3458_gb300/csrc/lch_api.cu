@@ -236,7 +236,15 @@ int run_pass(lch_ctx *ctx, int field, uint32_t h, uint32_t l, int inverse, const
     p.nlev = nlev;
     p.lg_cw = lg_cw;
     const uint64_t cols = S / (field / 8);
-    PROFM(LCH_KIND_PASS, 2ull * h * S, (uint64_t)(h / 2) * cols * nlev, launch_pass(field, p, s, &ctx->launches));
+    // multiplies executed: (h/2) per level, less the zero-factor butterflies
+    // the kernel skips (shift 0, the round over the transform's top levels:
+    // 2^i of them at level i, Sec. III.D)
+    uint64_t mults = (uint64_t)(h / 2) * nlev;
+    if (l == 0 && (1u << (L0 + nlev)) == h) {
+        const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, first = nlev > qa ? L0 + qa : L0;
+        mults -= (1ull << (L0 + nlev)) - (1ull << first);
+    }
+    PROFM(LCH_KIND_PASS, 2ull * h * S, mults * cols, launch_pass(field, p, s, &ctx->launches));
     return LCH_OK;
 }
 
