@@ -229,17 +229,18 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
 
-    # per-call latency (separate, event-timed)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
+    # per-call latency (separate, event-timed, at least 200 calls of each)
+    lat_reps = max(200, args.steps)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * lat_reps)]
     enc_ms, dec_ms = [], []
-    for i in range(args.steps):
+    for i in range(lat_reps):
         ev[3 * i].record(stream)
         ctx.rs_encode(n, k, r, buf)
         ev[3 * i + 1].record(stream)
         ctx.rs_decode(n, k, r, buf, mask)
         ev[3 * i + 2].record(stream)
     torch.cuda.synchronize()
-    for i in range(args.steps):
+    for i in range(lat_reps):
         enc_ms.append(ev[3 * i].elapsed_time(ev[3 * i + 1]))
         dec_ms.append(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]))
 
@@ -330,6 +331,7 @@ def run_ours(args):
     }
     if e2e:
         out["e2e"] = e2e
+    out["small_configs"] = run_small_latency(ctx, torch, rank)
     if not args.no_batch:
         out["batched"] = run_batch_compare(ctx, torch, args, rank)
     if not args.no_serve:
@@ -495,6 +497,42 @@ def run_serving(ctx, torch, args, rank):
     del pool
     torch.cuda.empty_cache()
     return out
+
+
+def run_small_latency(ctx, torch, rank, warmup=10, reps=200):
+    """Per-call latency of the two small workloads (small_gf8, medium_gf16),
+    where data volume is too small for an HBM fraction to mean much: 10
+    warm-up calls, then 200 encodes and 200 decodes, each timed with CUDA
+    events on the launch stream (inputs resident)."""
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name in ("small_gf8", "medium_gf16"):
+        w = WL.WORKLOADS[name]
+        r, n, k, S = w.field, w.n, w.k, w.shard_bytes
+        host = np.zeros((n, S), dtype=np.uint8)
+        host[:k] = WL.shards(k, S, w.seed + rank)
+        mask = WL.erasure_mask(n, w.erasures, w.seed + 100 + rank)
+        buf = torch.from_numpy(host).cuda()
+        for _ in range(warmup):
+            ctx.rs_encode(n, k, r, buf)
+            ctx.rs_decode(n, k, r, buf, mask)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * reps)]
+        for i in range(reps):
+            ev[3 * i].record(stream)
+            ctx.rs_encode(n, k, r, buf)
+            ev[3 * i + 1].record(stream)
+            ctx.rs_decode(n, k, r, buf, mask)
+            ev[3 * i + 2].record(stream)
+        torch.cuda.synchronize()
+        enc = [ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(reps)]
+        dec = [ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(reps)]
+        res[name] = {"n": n, "k": k, "shard_bytes": S, "erasures": int(mask.sum()), "calls": reps,
+                     "encode_ms_p50": round(pct(enc, 50), 4), "encode_ms_p99": round(pct(enc, 99), 4),
+                     "decode_ms_p50": round(pct(dec, 50), 4), "decode_ms_p99": round(pct(dec, 99), 4),
+                     "encode_gbs_p50": round(k * S / (pct(enc, 50) / 1e3) / 1e9, 2),
+                     "decode_gbs_p50": round(int(mask.sum()) * S / (pct(dec, 50) / 1e3) / 1e9, 2)}
+    return res
 
 
 def run_e2e(ctx, torch, host, mask, w, args):
