@@ -65,6 +65,7 @@ def parse():
     p.add_argument("--no-tune", action="store_true", help="keep the default pass plans (no lch_autotune)")
     p.add_argument("--tune-cache", default=None, help="JSON cache of tuned pass plans (read, and written if new)")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-small", action="store_true", help="skip the small-workload latency lines")
     p.add_argument("--serve-requests", type=int, default=1024)
     return p.parse_args()
 
@@ -331,7 +332,8 @@ def run_ours(args):
     }
     if e2e:
         out["e2e"] = e2e
-    out["small_configs"] = run_small_latency(ctx, torch, rank)
+    if not args.no_small:
+        out["small_configs"] = run_small_latency(ctx, torch, rank)
     if not args.no_batch:
         out["batched"] = run_batch_compare(ctx, torch, args, rank)
     if not args.no_serve:
