@@ -122,17 +122,17 @@ def test_medium_gf16_workload(ctx):
 
 
 def test_large_gf16_workload(ctx):
-    """n = 65536, k = 32768, 4 KiB shards: sampled parity rows and columns
-    against the oracle, then random and burst erasures of n - k rows recovered
+    """n = 65536, k = 32768, 4 KiB shards: all 32768 parity rows of 4 element
+    columns (the first, the last and two seeded ones) against the oracle's
+    Lagrange evaluation, then random and burst erasures of n - k rows recovered
     on every byte."""
     w = WL.WORKLOADS["large_gf16"]
     host = message(w.n, w.k, w.shard_bytes, w.seed)
     cw = gpu_encode(ctx, w.field, w.n, w.k, host)
     assert np.array_equal(cw[: w.k], host[: w.k])
-    cols = elem_cols(w.shard_bytes, w.field, 3, seed=3)
-    rows = np.sort(np.random.default_rng(4).choice(np.arange(w.k, w.n), 12, replace=False))
-    ref = O.rs_encode(w.field, w.n, w.k, elems(host, w.field, cols), rows=rows)
-    assert np.array_equal(elems(cw, w.field, cols)[rows], ref[rows])
+    cols = elem_cols(w.shard_bytes, w.field, 4, seed=3)
+    ref = O.rs_encode(w.field, w.n, w.k, elems(host, w.field, cols))
+    assert np.array_equal(elems(cw, w.field, cols), ref)
     for mask in (WL.erasure_mask(w.n, w.erasures, w.seed),
                  WL.burst_mask(w.n, w.erasures, 0),
                  WL.burst_mask(w.n, w.erasures, WL.random_burst_start(w.n, w.erasures, w.seed))):
