@@ -69,3 +69,22 @@ def test_python_binding_refuses_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(lch, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         lch.load()
+
+
+def test_utility_entry_points_check_arguments(L):
+    """Host-side checks of the entry points outside the paper (no GPU call is
+    made before a failing check)."""
+    vp = ctypes.c_void_p
+    assert L.lch_strerror(lch.LCH_ETIMEDOUT) == b"a batch task gave up waiting"
+    t = lch.Tuning()
+    assert L.lch_autotune(None, 16, 1024, 64, None, ctypes.byref(t)) == lch.LCH_EINVAL
+    assert L.lch_autotune(vp(1), 16, 1000, 64, None, ctypes.byref(t)) == lch.LCH_EINVAL   # h not a power of two
+    assert L.lch_autotune(vp(1), 16, 1024, 40, None, ctypes.byref(t)) == lch.LCH_EINVAL   # shard bytes
+    assert L.lch_tune_set(None, 16, 1024, 64, None) == lch.LCH_EINVAL
+    assert L.lch_tune_get(None, 16, 1024, 64, ctypes.byref(t)) == lch.LCH_EINVAL
+    assert L.lch_batch_set_wait_limit(None, 1000) == lch.LCH_EINVAL
+    assert L.lch_batch_selftest_stall(None, None) == lch.LCH_EINVAL
+    assert L.lch_rows_gather(None, vp(16), vp(16), 4, 64, None) == lch.LCH_EINVAL
+    assert L.lch_rows_scatter(vp(16), vp(16), vp(16), 4, 40, None) == lch.LCH_EINVAL
+    assert L.lch_rows_scatter(vp(8), vp(16), vp(16), 4, 64, None) == lch.LCH_EINVAL      # misaligned
+    assert L.lch_rows_gather(None, None, None, 0, 64, None) == lch.LCH_OK                 # count 0: no-op
