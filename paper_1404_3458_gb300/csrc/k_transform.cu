@@ -11,8 +11,14 @@
 // levels [L0, L0 + nlev) to tiles of 2^nlev rows whose row indices differ only
 // in bits L0 .. L0+nlev-1, so one HBM round trip covers up to 8 levels.  A tile
 // spans a slice of the shard columns; the factor records of its 2^nlev - 1
-// butterfly blocks are staged in shared memory once per CTA and reused for all
-// the column slices the CTA walks.
+// butterfly blocks are staged in shared memory once per row group a CTA
+// reaches and reused for all the column slices it walks.
+//
+// Kernels: k_pass_p / k_pass (transform passes, persistent and not), k_deriv_p
+// / k_deriv (formal derivative), k_rowscale (per-row constants), k_superset
+// (neighbour sums for the allocation-free derivative), k_batch (persistent
+// task queue over many codewords), k_pointwise (product of two vectors), and
+// small helpers (broadcast, row gather/scatter, fill).
 #include <algorithm>
 
 #include "lch_internal.cuh"
