@@ -543,13 +543,14 @@ def run_e2e(ctx, torch, host, mask, w, args):
     parity out; then it copies in the surviving shards (packed, with their
     row indices), scatters them into a codeword buffer (lch_rows_scatter),
     decodes, gathers the recovered rows (lch_rows_gather) and copies them out.
-    Steps are pipelined over two buffer sets and three streams (host-to-device
+    Steps are pipelined over NB buffer sets and three streams (host-to-device
     copies, compute, device-to-host copies), so one step's copies overlap the
-    previous step's kernels; each buffer is reused only after its last copy
-    out.  The last step's outputs are checked against the true codeword."""
+    neighbouring steps' kernels; each buffer is reused only after its last
+    copy out.  The last step's outputs are checked against the true codeword."""
     from paper_1404_3458_gb300 import lch
 
     r, n, k, S = w.field, w.n, w.k, w.shard_bytes
+    NB = 2
     erased = np.nonzero(mask)[0].astype(np.int32)
     surv = np.nonzero(mask == 0)[0].astype(np.int32)
     ne, ns = erased.size, surv.size
@@ -560,18 +561,18 @@ def run_e2e(ctx, torch, host, mask, w, args):
     del ref
     surv_host = truth[torch.from_numpy(surv).long()].contiguous().pin_memory()     # the received shards
     idx_host = torch.from_numpy(np.concatenate([surv, erased])).pin_memory()      # survivors, then erased rows
-    parity_out = [torch.empty((n - k, S), dtype=torch.uint8).pin_memory() for _ in range(2)]
-    rec_out = [torch.empty((ne, S), dtype=torch.uint8).pin_memory() for _ in range(2)]
-    enc = [torch.empty((n, S), dtype=torch.uint8, device="cuda") for _ in range(2)]
-    dec = [torch.empty((n, S), dtype=torch.uint8, device="cuda") for _ in range(2)]
-    pin_dev = [torch.empty((ns, S), dtype=torch.uint8, device="cuda") for _ in range(2)]
-    pout_dev = [torch.empty((ne, S), dtype=torch.uint8, device="cuda") for _ in range(2)]
-    idx_dev = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(2)]
+    parity_out = [torch.empty((n - k, S), dtype=torch.uint8).pin_memory() for _ in range(NB)]
+    rec_out = [torch.empty((ne, S), dtype=torch.uint8).pin_memory() for _ in range(NB)]
+    enc = [torch.empty((n, S), dtype=torch.uint8, device="cuda") for _ in range(NB)]
+    dec = [torch.empty((n, S), dtype=torch.uint8, device="cuda") for _ in range(NB)]
+    pin_dev = [torch.empty((ns, S), dtype=torch.uint8, device="cuda") for _ in range(NB)]
+    pout_dev = [torch.empty((ne, S), dtype=torch.uint8, device="cuda") for _ in range(NB)]
+    idx_dev = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(NB)]
     h2d, comp, d2h = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-    freed_e, freed_d = [None, None], [None, None]  # slot's last copy out has finished
+    freed_e, freed_d = [None] * NB, [None] * NB  # slot's last copy out has finished
 
     def step(i):
-        b = i & 1
+        b = i % NB
         ev = [torch.cuda.Event() for _ in range(4)]
         with torch.cuda.stream(h2d):
             if freed_e[b] is not None:
@@ -614,12 +615,12 @@ def run_e2e(ctx, torch, host, mask, w, args):
     z.record(d2h)
     torch.cuda.synchronize()
     ms = a.elapsed_time(z) / steps
-    last = (steps - 1) & 1
+    last = (steps - 1) % NB
     ok = bool(torch.equal(rec_out[last], truth[torch.from_numpy(erased).long()])) and \
         bool(torch.equal(parity_out[last], truth[k:]))
     return {"value": round((k + ne) * S / (ms / 1e3) / 1e9, 3), "unit": UNIT,
             "h2d_bytes_per_step": (k + ns) * S + 4 * n, "d2h_bytes_per_step": (n - k + ne) * S,
-            "ms_per_step": round(ms, 4), "pipelined": "2 buffer sets, 3 streams",
+            "ms_per_step": round(ms, 4), "pipelined": f"{NB} buffer sets, 3 streams",
             "received": "surviving shards only (packed, scattered on the device)", "verified": ok}
 
 
