@@ -33,6 +33,12 @@ constexpr uint32_t kTileBytes = 32768; // data bytes per tile
 constexpr int kTargetCtas = 152 * 8;
 constexpr int kSms = 152;
 constexpr size_t kPassSmem = 220 * 1024; // dynamic shared memory of the pass kernels
+#ifndef LCH_SPLIT_LG_CW
+#define LCH_SPLIT_LG_CW 8
+#endif
+// The persistent pass splits its CTA into two column halves from this tile
+// width (log2 bytes) up: a half-row must be at least one warp of words wide.
+constexpr uint32_t kSplitLgCw = LCH_SPLIT_LG_CW;
 
 
 // First record of local level s among the 2^nlev - 1 records of a tile.
@@ -217,17 +223,34 @@ struct TileOut {
     uint32_t L0, hibase, lo, width;
 };
 
+// The threads that share a tile and the column words they own: thread tid of
+// nthr takes words [wlo, wlo + 2^lg_wh) of every row; bar is the barrier they
+// meet at (0: the whole CTA, __syncthreads).  Columns are independent, so the
+// two halves of a CTA can run the two column halves of a tile each behind a
+// named barrier of its own and drift apart, which keeps the ALU pipe fed while
+// one half waits at a barrier.
+struct Lanes {
+    uint32_t tid, nthr, wlo, lg_wh, bar;
+};
+__device__ __forceinline__ Lanes lanes_all(uint32_t lg_w) { return {threadIdx.x, blockDim.x, 0u, lg_w, 0u}; }
+__device__ __forceinline__ void lanes_sync(const Lanes &ln)
+{
+    if (ln.bar == 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(ln.bar), "r"(ln.nthr) : "memory");
+}
+
 // GST = true: the round writes its results to global memory (the tile's last
 // round) instead of back to the tile.
 template <int R, int INV, int Q, bool GST, bool ZT>
 __device__ __forceinline__ void round_q(uint32_t data, uint32_t tab, uint32_t nrec, uint32_t nrows, uint32_t lg_w,
-                                        uint32_t s0, const TileOut &o)
+                                        uint32_t s0, const TileOut &o, const Lanes &ln)
 {
-    const uint32_t W = 1u << lg_w;
-    const uint32_t items = (nrows >> Q) << lg_w;
+    const uint32_t items = (nrows >> Q) << ln.lg_wh;
     const uint32_t stride = 4u << (s0 + lg_w); // bytes between the rows of a group
-    for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
-        const uint32_t g = it >> lg_w, w = it & (W - 1u);
+    for (uint32_t it = ln.tid; it < items; it += ln.nthr) {
+        const uint32_t g = it >> ln.lg_wh, w = ln.wlo + (it & ((1u << ln.lg_wh) - 1u));
         const uint32_t base = ((g >> s0) << (s0 + Q)) | (g & ((1u << s0) - 1u));
         const uint32_t p = data + (((base << lg_w) + w) << 2);
         uint32_t x[1 << Q];
@@ -250,13 +273,13 @@ __device__ __forceinline__ void round_q(uint32_t data, uint32_t tab, uint32_t nr
 
 template <int R, int INV, bool GST = false, bool ZT = false>
 __device__ __forceinline__ void run_round(uint32_t q, uint32_t data, uint32_t tab, uint32_t nrec, uint32_t nrows,
-                                          uint32_t lg_w, uint32_t s0, const TileOut &o = TileOut{})
+                                          uint32_t lg_w, uint32_t s0, const Lanes &ln, const TileOut &o = TileOut{})
 {
     switch (q) {
-    case 1: round_q<R, INV, 1, GST, ZT>(data, tab, nrec, nrows, lg_w, s0, o); break;
-    case 2: round_q<R, INV, 2, GST, ZT>(data, tab, nrec, nrows, lg_w, s0, o); break;
-    case 3: round_q<R, INV, 3, GST, ZT>(data, tab, nrec, nrows, lg_w, s0, o); break;
-    default: round_q<R, INV, 4, GST, ZT>(data, tab, nrec, nrows, lg_w, s0, o); break;
+    case 1: round_q<R, INV, 1, GST, ZT>(data, tab, nrec, nrows, lg_w, s0, o, ln); break;
+    case 2: round_q<R, INV, 2, GST, ZT>(data, tab, nrec, nrows, lg_w, s0, o, ln); break;
+    case 3: round_q<R, INV, 3, GST, ZT>(data, tab, nrec, nrows, lg_w, s0, o, ln); break;
+    default: round_q<R, INV, 4, GST, ZT>(data, tab, nrec, nrows, lg_w, s0, o, ln); break;
     }
 }
 
@@ -310,35 +333,35 @@ __device__ __forceinline__ void stage_pass_recs(const PassArgs &a, uint32_t nrow
 // round over the tile's top levels uses.
 template <int R, int INV>
 __device__ __forceinline__ void pass_tile(uint32_t sdata, uint32_t stab, uint32_t nlev, uint32_t lg_w, const TileOut &o,
-                                          bool zt)
+                                          bool zt, const Lanes &ln)
 {
     const uint32_t nrows = 1u << nlev, nrec = nrows - 1;
     const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, qb = nlev - qa;
     if (INV) {
         if (qb) {
-            run_round<R, INV>(qa, sdata, stab, nrec, nrows, lg_w, 0);
-            __syncthreads();
+            run_round<R, INV>(qa, sdata, stab, nrec, nrows, lg_w, 0, ln);
+            lanes_sync(ln);
             if (zt)
-                run_round<R, INV, true, true>(qb, sdata, stab, nrec, nrows, lg_w, qa, o);
+                run_round<R, INV, true, true>(qb, sdata, stab, nrec, nrows, lg_w, qa, ln, o);
             else
-                run_round<R, INV, true>(qb, sdata, stab, nrec, nrows, lg_w, qa, o);
+                run_round<R, INV, true>(qb, sdata, stab, nrec, nrows, lg_w, qa, ln, o);
         } else if (zt) {
-            run_round<R, INV, true, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, o);
+            run_round<R, INV, true, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, ln, o);
         } else {
-            run_round<R, INV, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, o);
+            run_round<R, INV, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, ln, o);
         }
     } else {
         if (qb) {
             if (zt)
-                run_round<R, INV, false, true>(qb, sdata, stab, nrec, nrows, lg_w, qa);
+                run_round<R, INV, false, true>(qb, sdata, stab, nrec, nrows, lg_w, qa, ln);
             else
-                run_round<R, INV>(qb, sdata, stab, nrec, nrows, lg_w, qa);
-            __syncthreads();
-            run_round<R, INV, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, o);
+                run_round<R, INV>(qb, sdata, stab, nrec, nrows, lg_w, qa, ln);
+            lanes_sync(ln);
+            run_round<R, INV, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, ln, o);
         } else if (zt) {
-            run_round<R, INV, true, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, o);
+            run_round<R, INV, true, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, ln, o);
         } else {
-            run_round<R, INV, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, o);
+            run_round<R, INV, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, ln, o);
         }
     }
 }
@@ -398,7 +421,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, uint32_t lg_cw, uin
             const size_t col = col0 + (size_t)t * col_step;
             const size_t rem = a.S - col;
             const TileOut o{a.dst, a.S, col, a.L0, hibase, lo, rem < cw ? (uint32_t)rem : cw};
-            pass_tile<R, INV>(sdata, stab, nlev, lg_w, o, zero_top(a));
+            pass_tile<R, INV>(sdata, stab, nlev, lg_w, o, zero_top(a), lanes_all(lg_w));
         }
         __syncthreads(); // everyone has read this buffer
         if (t + 2 < ntiles) issue(t + 2, data);
@@ -423,7 +446,12 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(PassArgs a, uint32_t l
 // (needs at least two tiles per group, so that at most two groups are live);
 // RB = 1: one record buffer, refilled when the CTA reaches a new group (a
 // short stall once per group, but room for wider tiles).
-template <int R, int INV, int RB>
+// SPLIT: the two halves of the CTA (256 threads each) take the two column
+// halves of every tile (tiles of at least 256 bytes, so a half-row is at
+// least one warp wide) and meet only at their own named barriers (1 and 2);
+// the whole CTA meets where factor records change hands (its first item and
+// every new group), because all of its threads copy the records in.
+template <int R, int INV, int RB, bool SPLIT>
 __device__ __forceinline__ void pass_items(const PassArgs &a, uint32_t lg_cw, uint32_t ntiles, uint32_t i0, uint32_t i1,
                                            uint8_t *sm)
 {
@@ -436,6 +464,11 @@ __device__ __forceinline__ void pass_items(const PassArgs &a, uint32_t lg_cw, ui
     if (i0 >= i1) return;
     const uint32_t g_first = i0 / ntiles + a.g0;
     auto rec_buf = [&](uint32_t g) -> uint32_t { return RB == 2 ? ((g - g_first) & 1u) * tab_sz : 0u; };
+    const uint32_t half = SPLIT ? threadIdx.x / (kPassThreads / 2) : 0u;
+    const Lanes ln = SPLIT ? Lanes{threadIdx.x % (kPassThreads / 2), kPassThreads / 2, half << (lg_w - 1), lg_w - 1, 1u + half}
+                           : lanes_all(lg_w);
+    // 16-byte chunks of a row that this thread's lanes copy: [c0, c0 + 2^lg_vh)
+    const uint32_t lg_vh = SPLIT ? lg_vpr - 1 : lg_vpr, c0 = half << lg_vh;
 
     // tile of item k into dstbuf (RB = 2: with its group's records when k opens a group)
     auto issue = [&](uint32_t k, uint8_t *dstbuf) {
@@ -446,11 +479,11 @@ __device__ __forceinline__ void pass_items(const PassArgs &a, uint32_t lg_cw, ui
         const size_t col = (size_t)t << lg_cw;
         const size_t rem = a.S - col;
         const uint32_t width = rem < cw ? (uint32_t)rem : cw;
-        for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
-            const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
+        for (uint32_t v = ln.tid; v < (nrows << lg_vh); v += ln.nthr) {
+            const uint32_t m = v >> lg_vh, c = c0 + (v & ((1u << lg_vh) - 1u));
             if (c * 16 < width) {
                 const size_t row = (hibase | ((size_t)m << a.L0) | lo) & a.src_mask;
-                cp_async16(dstbuf + v * 16, a.src + row * a.S + col + c * 16);
+                cp_async16(dstbuf + (((m << lg_vpr) + c) << 4), a.src + row * a.S + col + c * 16);
             }
         }
     };
@@ -468,24 +501,29 @@ __device__ __forceinline__ void pass_items(const PassArgs &a, uint32_t lg_cw, ui
         const uint32_t sdata = (uint32_t)__cvta_generic_to_shared(data);
         const uint32_t g = k / ntiles + a.g0, t = k - (k / ntiles) * ntiles;
         if (RB == 1 && k != i0 && t == 0) {
-            // new group: refill the record buffer (the previous item is done
-            // with it) and wait for it together with the tiles in flight
+            // new group: refill the record buffer once every thread is done
+            // with it, and wait for it together with the tiles in flight
+            if (SPLIT) __syncthreads();
             stage_pass_recs<R>(a, nrows, (g >> a.L0) << (a.L0 + nlev), sm);
             cp_async_commit();
             cp_async_wait_all();
+            __syncthreads();
         } else {
             cp_async_wait1(); // item k's tile and records have landed for this thread
+            if (!SPLIT || k == i0 || t == 0)
+                __syncthreads();
+            else
+                lanes_sync(ln);
         }
-        __syncthreads();
         {
             const uint32_t lo = g & ((1u << a.L0) - 1u);
             const uint32_t hibase = (g >> a.L0) << (a.L0 + nlev);
             const size_t col = (size_t)t << lg_cw;
             const size_t rem = a.S - col;
             const TileOut o{a.dst, a.S, col, a.L0, hibase, lo, rem < cw ? (uint32_t)rem : cw};
-            pass_tile<R, INV>(sdata, stab0 + rec_buf(g), nlev, lg_w, o, zero_top(a));
+            pass_tile<R, INV>(sdata, stab0 + rec_buf(g), nlev, lg_w, o, zero_top(a), ln);
         }
-        __syncthreads(); // everyone has read this tile and this group's records
+        lanes_sync(ln); // these lanes have read their part of this tile (and, unsplit, the group's records)
         if (k + 2 < i1) issue(k + 2, data);
         cp_async_commit();
     }
@@ -493,14 +531,14 @@ __device__ __forceinline__ void pass_items(const PassArgs &a, uint32_t lg_cw, ui
     __syncthreads();
 }
 
-template <int R, int INV, int RB>
+template <int R, int INV, int RB, bool SPLIT>
 __global__ void __launch_bounds__(kPassThreads, 1) k_pass_p(PassArgs a, uint32_t lg_cw, uint32_t ntiles, uint32_t items)
 {
     extern __shared__ __align__(128) uint8_t sm[];
     const uint32_t i0 = (uint32_t)((uint64_t)blockIdx.x * items / gridDim.x);
     const uint32_t i1 = (uint32_t)((uint64_t)(blockIdx.x + 1) * items / gridDim.x);
     pdl_trigger();
-    pass_items<R, INV, RB>(a, lg_cw, ntiles, i0, i1, sm);
+    pass_items<R, INV, RB, SPLIT>(a, lg_cw, ntiles, i0, i1, sm);
 }
 
 __global__ void __launch_bounds__(kThreads) k_superset(SupersetArgs a, uint32_t lg_cw)
@@ -1012,10 +1050,19 @@ cudaError_t pass_impl(const PassArgs &a, cudaStream_t s)
     if (ntiles >= 2 && items < (1ull << 32)) {
         // persistent form: two record sets when they fit beside the tiles
         const uint32_t ctas = (uint32_t)std::min<uint64_t>(items, kSms);
-        if (2 * tab + tiles <= kPassSmem)
-            return launch_pdl(k_pass_p<R, INV, 2>, dim3(ctas), dim3(kPassThreads), 2 * tab + tiles, s, a, lg_cw,
+        const bool two = 2 * tab + tiles <= kPassSmem;
+        const size_t smem = (two ? 2 : 1) * tab + tiles;
+        if (lg_cw >= kSplitLgCw) {
+            if (two)
+                return launch_pdl(k_pass_p<R, INV, 2, true>, dim3(ctas), dim3(kPassThreads), smem, s, a, lg_cw,
+                                  (uint32_t)ntiles, (uint32_t)items);
+            return launch_pdl(k_pass_p<R, INV, 1, true>, dim3(ctas), dim3(kPassThreads), smem, s, a, lg_cw,
                               (uint32_t)ntiles, (uint32_t)items);
-        return launch_pdl(k_pass_p<R, INV, 1>, dim3(ctas), dim3(kPassThreads), tab + tiles, s, a, lg_cw,
+        }
+        if (two)
+            return launch_pdl(k_pass_p<R, INV, 2, false>, dim3(ctas), dim3(kPassThreads), smem, s, a, lg_cw,
+                              (uint32_t)ntiles, (uint32_t)items);
+        return launch_pdl(k_pass_p<R, INV, 1, false>, dim3(ctas), dim3(kPassThreads), smem, s, a, lg_cw,
                           (uint32_t)ntiles, (uint32_t)items);
     }
     // About 4 tiles per CTA and at least ~6 CTAs per SM in total.
@@ -1233,14 +1280,22 @@ cudaError_t configure_transform_kernels()
     if ((e = cudaFuncSetAttribute(k_deriv_p<16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv_p<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv_p<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_p<8, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_p<8, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_p<16, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_p<16, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_p<8, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_p<8, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_p<16, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_p<16, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<8, 0, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<8, 0, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<8, 0, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<8, 0, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<8, 1, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<8, 1, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<8, 1, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<8, 1, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<16, 0, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<16, 0, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<16, 0, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<16, 0, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<16, 1, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<16, 1, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<16, 1, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_p<16, 1, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv<8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;

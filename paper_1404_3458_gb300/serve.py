@@ -10,9 +10,10 @@ Poisson stream) and are served on one GPU:
   request is launched at once as its own rs_encode/rs_decode call on a
   stream of its own, so a lightly loaded server answers as fast as one call;
 * continuous batching: once that stream is full and at least `min_batch`
-  requests wait, a free launch slot takes every admitted request that has not
-  started yet and plans it into one batch per operation (lch_batch_create_in,
-  memory from the arena), launched as a single persistent kernel while up to
+  requests wait, a free launch slot takes the waiting requests in arrival
+  order, up to `max_batch` of them and `max_batch_bytes` of codeword data,
+  and plans them into one batch per operation (lch_batch_create_in, memory
+  from the arena), launched as a single persistent kernel while up to
   `max_inflight` earlier batches are still running on other streams;
 * retirement: completed calls and batches are detected by polling their CUDA
   events; their requests get a completion time and their arena memory is
@@ -119,7 +120,8 @@ class _Inflight:
 
 class Server:
     def __init__(self, ctx: "lch.Context", budget_bytes: int, max_inflight: int = 3, max_batch: int = 1024,
-                 min_batch: int = 16, max_direct: int = 32, prefer_batch: bool = False):
+                 min_batch: int = 16, max_direct: int = 32, prefer_batch: bool = False,
+                 max_batch_bytes: int = 2 * 10**9):
         import torch
 
         self.torch = torch
@@ -131,6 +133,11 @@ class Server:
         self.min_batch = min_batch
         self.max_direct = max_direct
         self.prefer_batch = prefer_batch  # a backlog of min_batch goes to a free slot before the direct stream
+        # codeword bytes (n S summed) one batch may take, 0 = no limit.  A
+        # batch completes as a whole, so without a bound a deep backlog goes
+        # out as one long batch whose requests all wait for its end; too
+        # small a bound gives up the batch kernel's efficiency.
+        self.max_batch_bytes = max_batch_bytes
         self.streams = [torch.cuda.Stream() for _ in range(max_inflight)]
         # A lone request skips batch planning and runs as a single-codeword
         # call; each launch slot has its own context so those calls never
@@ -298,11 +305,16 @@ class Server:
                 stream = self.streams[slot]
                 admitted = []
                 room = self.arena.size - self.arena.used
+                work = 0
                 while waiting and len(admitted) < self.max_batch:
+                    w = waiting[0].n * waiting[0].shard_bytes
+                    if admitted and self.max_batch_bytes and work + w > self.max_batch_bytes:
+                        break
                     need = _estimate(waiting[0])
                     if need > room or not self._admit(waiting[0]):
                         break
                     room -= need
+                    work += w
                     admitted.append(waiting.popleft())
                 if not admitted and waiting and not inflight and not direct and _estimate(waiting[0]) > self.arena.size:
                     raise RuntimeError("a request does not fit in the serving memory budget")

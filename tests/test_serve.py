@@ -62,15 +62,16 @@ def _requests(ctx, count, rate, seed):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("budget_mb,rate,min_batch,max_direct", [(64, 20000.0, 16, 4), (8, 200000.0, 16, 4),
-                                                                  (64, 200000.0, 2, 0), (16, 50000.0, 4, 1)])
-def test_served_results_equal_alone(ctx, budget_mb, rate, min_batch, max_direct):
+@pytest.mark.parametrize("budget_mb,rate,min_batch,max_direct,max_batch_bytes",
+                         [(64, 20000.0, 16, 4, 0), (8, 200000.0, 16, 4, 0), (64, 200000.0, 2, 0, 0),
+                          (16, 50000.0, 4, 1, 0), (64, 200000.0, 2, 0, 1 << 19)])
+def test_served_results_equal_alone(ctx, budget_mb, rate, min_batch, max_direct, max_batch_bytes):
     import torch
 
-    reqs, expect = _requests(ctx, 60, rate, seed=budget_mb + min_batch)
+    reqs, expect = _requests(ctx, 60, rate, seed=budget_mb + min_batch + max_batch_bytes)
     got = {}
     server = SV.Server(ctx, budget_mb << 20, max_inflight=2, max_batch=32, min_batch=min_batch,
-                       max_direct=max_direct)
+                       max_direct=max_direct, max_batch_bytes=max_batch_bytes)
     stats = server.run(reqs, on_done=lambda r: got.__setitem__(r.rid, r.buf.clone()))
     torch.cuda.synchronize()
     assert len(got) == len(reqs)
