@@ -296,6 +296,7 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Shared-memory offset of chunk c (16 bytes) of record q among nrec records
@@ -855,21 +856,26 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_deriv(DerivArgs a, uint32_t
 
 // Persistent form (as k_pass_p with one record buffer): one CTA per SM walks a
 // contiguous range of (row group, column tile) items in group-major order,
-// refilling its per-row records when it reaches a new group; two stages of
-// (u tile, accumulator tile) double-buffer the loads.
+// refilling its per-row records when it reaches a new group.  Modes 0 and 2
+// load the u tile alone, through a ring of three slots beside one accumulator
+// tile, so two tiles are in flight while one is worked on; mode 1 loads u and
+// X (which becomes the accumulator) into two slots.  (An L2 prefetch of the
+// next item beyond those in flight made both modes slower.)
 template <int R, int MODE>
 __device__ __forceinline__ void deriv_items(const DerivArgs &a, uint32_t lg_cw, uint32_t ntiles, uint32_t i0, uint32_t i1,
                                             uint8_t *sm)
 {
     constexpr bool kX = MODE == 1, kMulB = MODE != 1;
+    constexpr uint32_t kRing = kX ? 2 : 3;
     const uint32_t nlev = a.nlev, nrows = 1u << nlev;
     const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
     const uint32_t rec_bytes = tab_bytes<R>(nrows);
     const uint32_t s_b = (uint32_t)__cvta_generic_to_shared(sm);
     const uint32_t s_binv = s_b + (kMulB ? rec_bytes : 0);
-    uint8_t *stage0 = sm + deriv_rec_bytes<R>(nrows, MODE);
+    uint8_t *ring0 = sm + deriv_rec_bytes<R>(nrows, MODE);
     const uint32_t tile_bytes = nrows << lg_cw;
-    const uint32_t stage_bytes = 2 * tile_bytes; // u tile + accumulator tile
+    const uint32_t slot_bytes = (kX ? 2 : 1) * tile_bytes;
+    const uint32_t sacc0 = (uint32_t)__cvta_generic_to_shared(ring0 + kRing * slot_bytes); // modes 0 and 2
     if (i0 >= i1) return;
     auto group = [&](uint32_t k, uint32_t &hibase, uint32_t &lo, uint32_t &t) {
         const uint32_t g = k / ntiles;
@@ -877,9 +883,13 @@ __device__ __forceinline__ void deriv_items(const DerivArgs &a, uint32_t lg_cw, 
         lo = g & ((1u << a.L0) - 1u);
         hibase = (g >> a.L0) << (a.L0 + nlev);
     };
-    auto issue = [&](uint32_t k, uint8_t *dstbuf) {
+    auto slot = [&](uint32_t k) { return ring0 + ((k - i0) % kRing) * slot_bytes; };
+    // item k's tile(s) into its slot
+    auto issue = [&](uint32_t k) {
+        if (k >= i1) return;
         uint32_t hibase, lo, t;
         group(k, hibase, lo, t);
+        uint8_t *dstbuf = slot(k);
         const size_t col = (size_t)t << lg_cw;
         const size_t rem = a.S - col;
         const uint32_t width = rem < cw ? (uint32_t)rem : cw;
@@ -898,20 +908,30 @@ __device__ __forceinline__ void deriv_items(const DerivArgs &a, uint32_t lg_cw, 
         stage_deriv_recs<R, MODE>(a, nrows, hibase, lo, sm); // static tables
     }
     pdl_wait(); // the predecessor's writes are visible from here on
-    issue(i0, stage0);
+    issue(i0);
     cp_async_commit();
-    if (i0 + 1 < i1) issue(i0 + 1, stage0 + stage_bytes);
+    issue(i0 + 1);
     cp_async_commit();
     for (uint32_t k = i0; k < i1; k++) {
-        uint8_t *stage = stage0 + ((k - i0) & 1u) * stage_bytes;
-        const uint32_t su = (uint32_t)__cvta_generic_to_shared(stage), sacc = su + tile_bytes;
+        const uint32_t su = (uint32_t)__cvta_generic_to_shared(slot(k));
+        const uint32_t sacc = kX ? su + tile_bytes : sacc0;
         uint32_t hibase, lo, t;
         group(k, hibase, lo, t);
         if (k != i0 && t == 0) {
-            // new group: refill the records (the previous item is done with them)
+            // new group: refill the records (every thread is done with them)
             stage_deriv_recs<R, MODE>(a, nrows, hibase, lo, sm);
             cp_async_commit();
-            cp_async_wait_all();
+            if constexpr (kRing == 3) {
+                issue(k + 2); // into the slot item k - 1 has left
+                cp_async_commit();
+                cp_async_wait1(); // the records and item k's tile (and k + 1's)
+            } else {
+                cp_async_wait_all();
+            }
+        } else if constexpr (kRing == 3) {
+            issue(k + 2);
+            cp_async_commit();
+            cp_async_wait2(); // item k's tile (and, for k = i0, the records)
         } else {
             cp_async_wait1();
         }
@@ -920,8 +940,10 @@ __device__ __forceinline__ void deriv_items(const DerivArgs &a, uint32_t lg_cw, 
         const size_t rem = a.S - col;
         deriv_tile<R, MODE>(a, su, sacc, s_b, s_binv, lg_w, hibase, lo, col, rem < cw ? (uint32_t)rem : cw);
         __syncthreads();
-        if (k + 2 < i1) issue(k + 2, stage);
-        cp_async_commit();
+        if constexpr (kRing == 2) {
+            issue(k + 2);
+            cp_async_commit();
+        }
     }
     cp_async_wait_all();
     __syncthreads();
@@ -964,29 +986,35 @@ __global__ void __launch_bounds__(kThreads)
                int skip_zero)
 {
     __shared__ __align__(128) uint8_t T[kRowsPerCta * FT<R>::rec_bytes];
-    __shared__ uint32_t ks[kRowsPerCta];
     pdl_trigger();
     pdl_wait(); // coef and src come from predecessors
     const uint32_t r0 = blockIdx.x * kRowsPerCta;
     constexpr uint32_t cpr = FT<R>::rec_bytes / 16;
-    for (uint32_t v = threadIdx.x; v < kRowsPerCta * cpr; v += blockDim.x) {
-        const uint32_t q = v / cpr, c = v - q * cpr;
-        const uint32_t k = r0 + q < rows ? coef[r0 + q] : 0u;
-        *reinterpret_cast<uint4 *>(T + rec_dst<R>(kRowsPerCta, q, c)) = rec_chunk<R>(k, c);
-        if (c == 0) ks[q] = k;
-    }
-    __syncthreads();
     uint32_t k[kRowsPerCta];
 #pragma unroll
-    for (uint32_t q = 0; q < kRowsPerCta; q++) k[q] = ks[q];
-    const TabRef<R> t = tab_ref<R>((uint32_t)__cvta_generic_to_shared(T), 0, kRowsPerCta);
+    for (uint32_t q = 0; q < kRowsPerCta; q++) k[q] = r0 + q < rows ? coef[r0 + q] : 0u;
     const size_t vpr = S / 16;
     const uint4 *s4 = reinterpret_cast<const uint4 *>(src) + (size_t)r0 * vpr;
     uint4 *d4 = reinterpret_cast<uint4 *>(dst) + (size_t)r0 * vpr;
-    for (size_t i = threadIdx.x; i < vpr; i += blockDim.x) {
-        uint4 x[kRowsPerCta];
+    // the first slice's rows are read before the tables are built, so the
+    // loads are in flight meanwhile
+    uint4 x[kRowsPerCta];
+    if (threadIdx.x < vpr) {
 #pragma unroll
-        for (uint32_t q = 0; q < kRowsPerCta; q++) x[q] = k[q] ? s4[q * vpr + i] : make_uint4(0, 0, 0, 0);
+        for (uint32_t q = 0; q < kRowsPerCta; q++) x[q] = k[q] ? s4[q * vpr + threadIdx.x] : make_uint4(0, 0, 0, 0);
+    }
+    for (uint32_t v = threadIdx.x; v < kRowsPerCta * cpr; v += blockDim.x) {
+        const uint32_t q = v / cpr, c = v - q * cpr;
+        const uint32_t kq = r0 + q < rows ? coef[r0 + q] : 0u;
+        *reinterpret_cast<uint4 *>(T + rec_dst<R>(kRowsPerCta, q, c)) = rec_chunk<R>(kq, c);
+    }
+    __syncthreads();
+    const TabRef<R> t = tab_ref<R>((uint32_t)__cvta_generic_to_shared(T), 0, kRowsPerCta);
+    for (size_t i = threadIdx.x; i < vpr; i += blockDim.x) {
+        if (i != threadIdx.x) {
+#pragma unroll
+            for (uint32_t q = 0; q < kRowsPerCta; q++) x[q] = k[q] ? s4[q * vpr + i] : make_uint4(0, 0, 0, 0);
+        }
         RowsScale<R>::run(x, k, t);
 #pragma unroll
         for (uint32_t q = 0; q < kRowsPerCta; q++)
