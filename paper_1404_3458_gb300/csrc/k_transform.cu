@@ -375,8 +375,10 @@ __device__ __forceinline__ bool zero_top(const PassArgs &a)
 
 // One CTA walks the column tiles [y0, y0 + ystep, ...) of row group g: the
 // group's factor records stay in shared memory; tile t+1 is copied in
-// (cp.async) while tile t is transformed.
-template <int R, int INV>
+// (cp.async) while tile t is transformed.  SPLIT: as in pass_items below, the
+// two halves of the CTA take the two column halves of each tile and meet at
+// their own barriers after the first tile.
+template <int R, int INV, bool SPLIT>
 __device__ __forceinline__ void pass_body(const PassArgs &a, uint32_t lg_cw, uint32_t g, uint32_t y0, uint32_t ystep,
                                           uint8_t *sm)
 {
@@ -391,40 +393,47 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, uint32_t lg_cw, uin
     const size_t col_step = (size_t)ystep << lg_cw;
     const size_t col0 = (size_t)y0 << lg_cw;
     const uint32_t ntiles = col0 < a.S ? (uint32_t)((a.S - col0 + col_step - 1) / col_step) : 0;
+    const uint32_t half = SPLIT ? threadIdx.x / (kPassThreads / 2) : 0u;
+    const Lanes ln = SPLIT ? Lanes{threadIdx.x % (kPassThreads / 2), kPassThreads / 2, half << (lg_w - 1), lg_w - 1, 1u + half}
+                           : lanes_all(lg_w);
+    const uint32_t lg_vh = SPLIT ? lg_vpr - 1 : lg_vpr, c0 = half << lg_vh;
 
     stage_pass_recs<R>(a, nrows, hibase, sm); // first copy group (static tables)
     pdl_wait(); // the predecessor's writes are visible from here on
 
-    auto issue = [&](uint32_t t, uint32_t *dstbuf) {
+    auto issue = [&](uint32_t t, uint8_t *dstbuf) {
         const size_t col = col0 + (size_t)t * col_step;
         const size_t rem = a.S - col;
         const uint32_t width = rem < cw ? (uint32_t)rem : cw;
-        for (uint32_t v = threadIdx.x; v < (nrows << lg_vpr); v += blockDim.x) {
-            const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
+        for (uint32_t v = ln.tid; v < (nrows << lg_vh); v += ln.nthr) {
+            const uint32_t m = v >> lg_vh, c = c0 + (v & ((1u << lg_vh) - 1u));
             if (c * 16 < width) {
                 const size_t row = (hibase | ((size_t)m << a.L0) | lo) & a.src_mask;
-                cp_async16(reinterpret_cast<uint8_t *>(dstbuf) + v * 16, a.src + row * a.S + col + c * 16);
+                cp_async16(dstbuf + (((m << lg_vpr) + c) << 4), a.src + row * a.S + col + c * 16);
             }
         }
     };
 
-    if (ntiles > 0) issue(0, reinterpret_cast<uint32_t *>(buf0));
+    if (ntiles > 0) issue(0, buf0);
     cp_async_commit();
-    if (ntiles > 1) issue(1, reinterpret_cast<uint32_t *>(buf0 + tile_bytes));
+    if (ntiles > 1) issue(1, buf0 + tile_bytes);
     cp_async_commit();
 
     for (uint32_t t = 0; t < ntiles; t++) {
-        uint32_t *data = reinterpret_cast<uint32_t *>(buf0 + (t & 1u) * tile_bytes);
+        uint8_t *data = buf0 + (t & 1u) * tile_bytes;
         const uint32_t sdata = (uint32_t)__cvta_generic_to_shared(data);
         cp_async_wait1(); // tile t (and the records) have landed for this thread
-        __syncthreads();
+        if (!SPLIT || t == 0)
+            __syncthreads();
+        else
+            lanes_sync(ln);
         {
             const size_t col = col0 + (size_t)t * col_step;
             const size_t rem = a.S - col;
             const TileOut o{a.dst, a.S, col, a.L0, hibase, lo, rem < cw ? (uint32_t)rem : cw};
-            pass_tile<R, INV>(sdata, stab, nlev, lg_w, o, zero_top(a), lanes_all(lg_w));
+            pass_tile<R, INV>(sdata, stab, nlev, lg_w, o, zero_top(a), ln);
         }
-        __syncthreads(); // everyone has read this buffer
+        lanes_sync(ln); // these lanes have read their part of this buffer
         if (t + 2 < ntiles) issue(t + 2, data);
         cp_async_commit();
     }
@@ -437,7 +446,10 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(PassArgs a, uint32_t l
 {
     extern __shared__ __align__(128) uint8_t sm[];
     pdl_trigger();
-    pass_body<R, INV>(a, lg_cw, blockIdx.x, blockIdx.y, gridDim.y, sm);
+    if (lg_cw >= kSplitLgCw)
+        pass_body<R, INV, true>(a, lg_cw, blockIdx.x, blockIdx.y, gridDim.y, sm);
+    else
+        pass_body<R, INV, false>(a, lg_cw, blockIdx.x, blockIdx.y, gridDim.y, sm);
 }
 
 // Persistent form: one CTA per SM takes a contiguous range of the
@@ -1165,11 +1177,19 @@ __device__ __forceinline__ void run_task(const BatchOp &op, const BatchTask &t, 
     case kOpRows: rows_body<R>(op, t.g0, t.g1, sm); break;
     case kOpPass: {
         PassArgs a{op.src, op.dst, op.S, op.h, op.L0, op.nlev, op.l, (int)op.mode, op.tab0};
+        const bool split = op.lg_cw >= kSplitLgCw;
         for (uint32_t g = t.g0; g < t.g1; g++)
-            if (op.mode)
-                pass_body<R, 1>(a, op.lg_cw, g, 0, 1, sm);
-            else
-                pass_body<R, 0>(a, op.lg_cw, g, 0, 1, sm);
+            if (op.mode) {
+                if (split)
+                    pass_body<R, 1, true>(a, op.lg_cw, g, 0, 1, sm);
+                else
+                    pass_body<R, 1, false>(a, op.lg_cw, g, 0, 1, sm);
+            } else {
+                if (split)
+                    pass_body<R, 0, true>(a, op.lg_cw, g, 0, 1, sm);
+                else
+                    pass_body<R, 0, false>(a, op.lg_cw, g, 0, 1, sm);
+            }
         break;
     }
     default: {
