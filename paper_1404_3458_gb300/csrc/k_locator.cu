@@ -30,6 +30,8 @@ __global__ void __launch_bounds__(1024) k_loc_small(uint32_t lgn, MaskBits bits,
                                                     uint32_t *fl_out, uint16_t *pre, uint16_t *post, uint32_t ninv)
 {
     extern __shared__ uint32_t v[];
+    pdl_trigger();
+    pdl_wait(); // a predecessor may still read pre/post or the work array
     const uint32_t n = 1u << lgn;
     for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) v[j] = MODE == 0 ? (j ? logt[j] : 0u) : mask_bit(bits, j);
     __syncthreads();
@@ -51,6 +53,8 @@ __global__ void __launch_bounds__(256) k_loc_a(uint32_t a, MaskBits bits, const 
                                                uint32_t *work)
 {
     extern __shared__ uint32_t v[];
+    pdl_trigger();
+    pdl_wait(); // a predecessor may still read the work array
     const uint32_t base = blockIdx.x << a, len = 1u << a;
     for (uint32_t u = threadIdx.x; u < len; u += blockDim.x) {
         uint32_t j = base + u;
@@ -69,6 +73,8 @@ __global__ void __launch_bounds__(256) k_loc_b(uint32_t a, uint32_t b, const uin
                                                const uint32_t *in, uint32_t *out)
 {
     extern __shared__ uint32_t v[];
+    pdl_trigger();
+    pdl_wait(); // in comes from the predecessor
     const uint32_t lo = blockIdx.x, len = 1u << b;
     for (uint32_t u = threadIdx.x; u < len; u += blockDim.x) v[u] = in[(u << a) | lo];
     __syncthreads();
@@ -88,6 +94,8 @@ __global__ void __launch_bounds__(256) k_loc_c(uint32_t a, MaskBits bits, const 
                                                uint32_t ninv, const uint32_t *work, uint16_t *pre, uint16_t *post)
 {
     extern __shared__ uint32_t v[];
+    pdl_trigger();
+    pdl_wait(); // work comes from the predecessor
     const uint32_t base = blockIdx.x << a, len = 1u << a;
     for (uint32_t u = threadIdx.x; u < len; u += blockDim.x) v[u] = work[base + u];
     __syncthreads();
@@ -108,30 +116,35 @@ cudaError_t run(int mode, const FieldTables &t, uint32_t lgn, const MaskBits *bi
     const uint32_t ninv = (uint32_t)((1ull << (R - lgn)) % M);
     static const MaskBits zero_bits = {};
     const MaskBits &mb = bits ? *bits : zero_bits;
+    cudaError_t e;
     if (lgn <= kSmallLg) {
         const uint32_t n = 1u << lgn;
         const unsigned threads = n < 1024 ? (n < 32 ? 32 : n) : 1024;
         const size_t smem = sizeof(uint32_t) * n;
         if (mode == 0)
-            k_loc_small<R, 0><<<1, threads, smem, s>>>(lgn, mb, t.logt, t.expt, fl, fl_out, pre, post, ninv);
+            e = launch_pdl(k_loc_small<R, 0>, dim3(1), dim3(threads), smem, s, lgn, mb, t.logt, t.expt, fl, fl_out, pre, post, ninv);
         else
-            k_loc_small<R, 1><<<1, threads, smem, s>>>(lgn, mb, t.logt, t.expt, fl, fl_out, pre, post, ninv);
+            e = launch_pdl(k_loc_small<R, 1>, dim3(1), dim3(threads), smem, s, lgn, mb, t.logt, t.expt, fl, fl_out, pre, post, ninv);
         *launches += 1;
-        return cudaGetLastError();
+        return e;
     }
     const uint32_t a = (lgn + 1) / 2, b = lgn - a;
     const size_t sa = sizeof(uint32_t) << a, sb = sizeof(uint32_t) << b;
     if (mode == 0) { // FWHT(L) = FWHT_high(FWHT_low(L))
-        k_loc_a<R, 0><<<1u << b, 256, sa, s>>>(a, mb, t.logt, work);
-        k_loc_b<R, 0><<<1u << a, 256, sb, s>>>(a, b, fl, work, fl_out);
-        *launches += 2;
-        return cudaGetLastError();
+        if ((e = launch_pdl(k_loc_a<R, 0>, dim3(1u << b), dim3(256), sa, s, a, mb, t.logt, work))) return e;
+        *launches += 1;
+        e = launch_pdl(k_loc_b<R, 0>, dim3(1u << a), dim3(256), sb, s, a, b, fl, (const uint32_t *)work, fl_out);
+        *launches += 1;
+        return e;
     }
-    k_loc_a<R, 1><<<1u << b, 256, sa, s>>>(a, mb, t.logt, work);
-    k_loc_b<R, 1><<<1u << a, 256, sb, s>>>(a, b, fl, work, work);
-    k_loc_c<R><<<1u << b, 256, sa, s>>>(a, mb, t.expt, ninv, work, pre, post);
-    *launches += 3;
-    return cudaGetLastError();
+    if ((e = launch_pdl(k_loc_a<R, 1>, dim3(1u << b), dim3(256), sa, s, a, mb, t.logt, work))) return e;
+    *launches += 1;
+    if ((e = launch_pdl(k_loc_b<R, 1>, dim3(1u << a), dim3(256), sb, s, a, b, fl, (const uint32_t *)work, work)))
+        return e;
+    *launches += 1;
+    e = launch_pdl(k_loc_c<R>, dim3(1u << b), dim3(256), sa, s, a, mb, t.expt, ninv, (const uint32_t *)work, pre, post);
+    *launches += 1;
+    return e;
 }
 
 } // namespace

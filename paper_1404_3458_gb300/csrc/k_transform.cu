@@ -1034,6 +1034,240 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// ------------------------------------------------ fused decode of short codewords
+// When lg n <= 8 every transform of Algorithm 2 fits one tile, so one CTA per
+// column slice runs the whole decode in shared memory after the locator:
+//   Phi = F . Pi on the surviving rows, 0 on the erased ones (eq. hatF(l));
+//   the coefficients (Psi_n^0)^-1 [Phi];
+//   the formal derivative: u = B . phi, the neighbour sums of Sec. IV, B^-1;
+//   Psi_n^0 of the result; and F(j) = hatF'(j) / Pi'(j) on the erased rows.
+// Shared memory: the factor records of Psi_n^0 (n - 1, kept for both
+// transforms), one per-row record set (Pi, B, B^-1 and 1/Pi' in turn), the
+// data tile and the derivative's accumulator tile, each n rows x 2^lg_cw bytes.
+struct FusedDecArgs {
+    uint8_t *shards;
+    size_t S;
+    uint32_t lgn;
+    const uint8_t *rec;             // factor records of every level
+    const uint8_t *brec, *binvrec;  // records of B_j and B_j^-1
+    const uint16_t *pre, *post;     // Pi(j) off E (0 on E); 1/Pi'(j) on E (0 off E)
+};
+
+template <int R>
+__host__ __device__ __forceinline__ size_t fused_dec_smem(uint32_t lgn, uint32_t lg_cw)
+{
+    const uint32_t n = 1u << lgn;
+    return (size_t)tab_bytes<R>(n - 1) + tab_bytes<R>(n) + (2ull * n << lg_cw);
+}
+
+// x_row <- c_row x_row for every word of the tile, c_row's record at row in srec.
+template <int R>
+__device__ __forceinline__ void tile_rows_mul(uint32_t sdata, uint32_t srec, uint32_t n, uint32_t lg_w)
+{
+    for (uint32_t it = threadIdx.x; it < (n << lg_w); it += blockDim.x) {
+        const uint32_t p = sdata + (it << 2);
+        sts_u32(p, MulK<R, 0>::f(lds_u32(p), tab_ref<R>(srec, it >> lg_w, n)));
+    }
+}
+
+// All nlev levels of a shift-0 transform on the tile (as pass_tile, every
+// round writing back to the tile).
+template <int R, int INV>
+__device__ __forceinline__ void tile_levels(uint32_t sdata, uint32_t stab, uint32_t nlev, uint32_t lg_w)
+{
+    const uint32_t nrows = 1u << nlev, nrec = nrows - 1;
+    const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, qb = nlev - qa;
+    const Lanes ln = lanes_all(lg_w);
+    if (INV) {
+        if (qb) {
+            run_round<R, INV>(qa, sdata, stab, nrec, nrows, lg_w, 0, ln);
+            __syncthreads();
+            run_round<R, INV, false, true>(qb, sdata, stab, nrec, nrows, lg_w, qa, ln);
+        } else {
+            run_round<R, INV, false, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, ln);
+        }
+    } else {
+        if (qb) {
+            run_round<R, INV, false, true>(qb, sdata, stab, nrec, nrows, lg_w, qa, ln);
+            __syncthreads();
+            run_round<R, INV>(qa, sdata, stab, nrec, nrows, lg_w, 0, ln);
+        } else {
+            run_round<R, INV, false, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, ln);
+        }
+    }
+}
+
+// Neighbour sums of the derivative over all lgn bits: acc_j = XOR of u_{j+2^l}
+// over the bits l clear in j (u in su, the sums in sacc).
+template <int R>
+__device__ __forceinline__ void tile_nbr_sums(uint32_t su, uint32_t sacc, uint32_t lgn, uint32_t lg_w)
+{
+    const DerivArgs d{};
+    const uint32_t n = 1u << lgn;
+#define LCH_NS(Q, S0, F) deriv_round<R, Q, S0, F, false, false, false, false, false>(d, su, sacc, 0, 0, n, lg_w, 0, 0, 0, 0)
+    switch (lgn) {
+    case 1: LCH_NS(1, 0, true); break;
+    case 2: LCH_NS(2, 0, true); break;
+    case 3: LCH_NS(3, 0, true); break;
+    case 4: LCH_NS(4, 0, true); break;
+    case 5: LCH_NS(3, 0, true); __syncthreads(); LCH_NS(2, 3, false); break;
+    case 6: LCH_NS(3, 0, true); __syncthreads(); LCH_NS(3, 3, false); break;
+    case 7: LCH_NS(4, 0, true); __syncthreads(); LCH_NS(3, 4, false); break;
+    default: LCH_NS(4, 0, true); __syncthreads(); LCH_NS(4, 4, false); break;
+    }
+#undef LCH_NS
+}
+
+template <int R>
+__global__ void __launch_bounds__(kPassThreads, 1) k_fused_dec(FusedDecArgs a, uint32_t lg_cw)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
+    constexpr uint32_t cpr = FT<R>::rec_bytes / 16;
+    const uint32_t lgn = a.lgn, n = 1u << lgn;
+    const uint32_t lg_w = lg_cw - 2, lg_vpr = lg_cw - 4, cw = 1u << lg_cw;
+    uint8_t *rrec = sm + tab_bytes<R>(n - 1);
+    uint8_t *t0 = rrec + tab_bytes<R>(n);
+    uint8_t *t1 = t0 + (n << lg_cw);
+    const uint32_t sf = (uint32_t)__cvta_generic_to_shared(sm), sr = (uint32_t)__cvta_generic_to_shared(rrec);
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(t0), s1 = (uint32_t)__cvta_generic_to_shared(t1);
+    const size_t col = (size_t)blockIdx.x << lg_cw;
+    const size_t rem = a.S - col;
+    const uint32_t width = rem < cw ? (uint32_t)rem : cw;
+
+    pdl_trigger();
+    {
+        PassArgs p{};
+        p.rec = a.rec;
+        p.L0 = 0;
+        p.l = 0;
+        stage_pass_recs<R>(p, n, 0, sm); // static tables
+    }
+    pdl_wait(); // pre/post and the shards come from predecessors
+
+    // Phi = F . Pi: survivors in, erased rows (and the ragged tail) zero
+    for (uint32_t v = threadIdx.x; v < (n << lg_vpr); v += blockDim.x) {
+        const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
+        if (a.pre[m] != 0 && c * 16 < width)
+            cp_async16(t0 + v * 16, a.shards + (size_t)m * a.S + col + c * 16);
+        else
+            *reinterpret_cast<uint4 *>(t0 + v * 16) = make_uint4(0, 0, 0, 0);
+    }
+    cp_async_commit();
+    for (uint32_t v = threadIdx.x; v < n * cpr; v += blockDim.x) {
+        const uint32_t q = v / cpr, c = v - q * cpr;
+        *reinterpret_cast<uint4 *>(rrec + rec_dst<R>(n, q, c)) = rec_chunk<R>(a.pre[q], c);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    tile_rows_mul<R>(s0, sr, n, lg_w);
+    __syncthreads();
+    // the records of B, copied in while the inverse transform runs
+    for (uint32_t v = threadIdx.x; v < n * cpr; v += blockDim.x) {
+        const uint32_t q = v / cpr, c = v - q * cpr;
+        cp_async16(rrec + rec_dst<R>(n, q, c), a.brec + (size_t)q * FT<R>::rec_bytes + c * 16);
+    }
+    cp_async_commit();
+    tile_levels<R, 1>(s0, sf, lgn, lg_w); // Algorithm 2: coefficients of hatF
+    cp_async_wait_all();
+    __syncthreads();
+    tile_rows_mul<R>(s0, sr, n, lg_w); // u = B . phi
+    __syncthreads();
+    for (uint32_t v = threadIdx.x; v < n * cpr; v += blockDim.x) {
+        const uint32_t q = v / cpr, c = v - q * cpr;
+        cp_async16(rrec + rec_dst<R>(n, q, c), a.binvrec + (size_t)q * FT<R>::rec_bytes + c * 16);
+    }
+    cp_async_commit();
+    tile_nbr_sums<R>(s0, s1, lgn, lg_w);
+    cp_async_wait_all();
+    __syncthreads();
+    tile_rows_mul<R>(s1, sr, n, lg_w); // the derivative's coefficients, B^-1 (sums)
+    __syncthreads();
+    for (uint32_t v = threadIdx.x; v < n * cpr; v += blockDim.x) {
+        const uint32_t q = v / cpr, c = v - q * cpr;
+        *reinterpret_cast<uint4 *>(rrec + rec_dst<R>(n, q, c)) = rec_chunk<R>(a.post[q], c);
+    }
+    tile_levels<R, 0>(s1, sf, lgn, lg_w); // hatF' at every point
+    __syncthreads();
+    // F(j) = hatF'(j) / Pi'(j), written to the erased rows only
+    for (uint32_t it = threadIdx.x; it < (n << lg_w); it += blockDim.x) {
+        const uint32_t row = it >> lg_w, w = it & ((1u << lg_w) - 1u);
+        if (a.post[row] != 0 && w * 4 < width) {
+            const uint32_t x = MulK<R, 0>::f(lds_u32(s1 + (it << 2)), tab_ref<R>(sr, row, n));
+            *reinterpret_cast<uint32_t *>(a.shards + (size_t)row * a.S + col + w * 4) = x;
+        }
+    }
+}
+
+// ------------------------------------------------ fused encode of short messages
+// Algorithm 1 for lg k <= 8 in one launch: one CTA per column slice holds the
+// k message rows, runs bar M_k = (Psi_k^0)^-1 [M_k] in shared memory, then for
+// each coset i = 1 .. n/k - 1 transforms a copy with Psi_k^{ik} and writes it
+// to rows ik .. ik + k - 1.  Shared memory: the factor records of Psi_k^0 and
+// of the current coset's Psi_k^{ik}, bar M_k and the working copy.
+struct FusedEncArgs {
+    uint8_t *shards;
+    size_t S;
+    uint32_t lgk, ncos; // ncos = n / k - 1 cosets
+    const uint8_t *rec;
+};
+
+template <int R>
+__host__ __device__ __forceinline__ size_t fused_enc_smem(uint32_t lgk, uint32_t lg_cw)
+{
+    const uint32_t k = 1u << lgk;
+    return 2ull * tab_bytes<R>(k - 1) + (2ull * k << lg_cw);
+}
+
+template <int R>
+__global__ void __launch_bounds__(kPassThreads, 1) k_fused_enc(FusedEncArgs a, uint32_t lg_cw)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
+    const uint32_t lgk = a.lgk, k = 1u << lgk;
+    const uint32_t lg_w = lg_cw - 2, lg_vpr = lg_cw - 4, cw = 1u << lg_cw;
+    const uint32_t ftab = tab_bytes<R>(k - 1), tile = k << lg_cw;
+    uint8_t *fcos = sm + ftab;
+    uint8_t *tm = fcos + ftab, *tw = tm + tile;
+    const uint32_t sf = (uint32_t)__cvta_generic_to_shared(sm), sc = (uint32_t)__cvta_generic_to_shared(fcos);
+    const uint32_t sm_m = (uint32_t)__cvta_generic_to_shared(tm), sw = (uint32_t)__cvta_generic_to_shared(tw);
+    const size_t col = (size_t)blockIdx.x << lg_cw;
+    const size_t rem = a.S - col;
+    const uint32_t width = rem < cw ? (uint32_t)rem : cw;
+    PassArgs p{};
+    p.rec = a.rec;
+    p.L0 = 0;
+
+    pdl_trigger();
+    p.l = 0;
+    stage_pass_recs<R>(p, k, 0, sm); // static tables: Psi_k^0 and the first coset
+    p.l = k;
+    stage_pass_recs<R>(p, k, 0, fcos);
+    pdl_wait(); // the message rows may come from a predecessor
+    for (uint32_t v = threadIdx.x; v < (k << lg_vpr); v += blockDim.x) {
+        const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
+        if (c * 16 < width) cp_async16(tm + v * 16, a.shards + (size_t)m * a.S + col + c * 16);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    tile_levels<R, 1>(sm_m, sf, lgk, lg_w); // Algorithm 1, line 1
+    __syncthreads();
+    for (uint32_t i = 1; i <= a.ncos; i++) {
+        if (i > 1) { // the previous coset is done with its records
+            p.l = i << lgk;
+            stage_pass_recs<R>(p, k, 0, fcos);
+            cp_async_commit();
+        }
+        for (uint32_t v = threadIdx.x; v < (tile >> 4); v += blockDim.x)
+            reinterpret_cast<uint4 *>(tw)[v] = reinterpret_cast<const uint4 *>(tm)[v];
+        cp_async_wait_all();
+        __syncthreads();
+        // lines 2-4: bar F_i = Psi_k^{ik} [bar M_k], stored to rows ik ..
+        const TileOut o{a.shards, a.S, col, 0, i << lgk, 0, width};
+        pass_tile<R, 0>(sw, sc, lgk, lg_w, o, false, lanes_all(lg_w));
+        __syncthreads();
+    }
+}
+
 uint32_t ilog2(uint64_t x)
 {
     uint32_t l = 0;
@@ -1350,6 +1584,10 @@ cudaError_t configure_transform_kernels()
     if ((e = cudaFuncSetAttribute(k_deriv<16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_fused_enc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_fused_enc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_fused_dec<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_fused_dec<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes())))
         return e;
     return cudaFuncSetAttribute(k_superset, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -1506,6 +1744,61 @@ cudaError_t launch_deriv(int r, int mode, const DerivArgs &a, cudaStream_t s, ui
     *launches += 1;
     if (r == 8) return mode == 0 ? deriv_impl<8, 0>(a, s) : mode == 1 ? deriv_impl<8, 1>(a, s) : deriv_impl<8, 2>(a, s);
     return mode == 0 ? deriv_impl<16, 0>(a, s) : mode == 1 ? deriv_impl<16, 1>(a, s) : deriv_impl<16, 2>(a, s);
+}
+
+uint32_t fused_dec_lg_cw(int r, uint32_t lgn, size_t S)
+{
+    if (lgn < 1 || lgn > 8) return 0;
+    uint32_t fit = 3;
+    while (fit < 12 && (1ull << (fit + 1)) < 2 * S &&
+           (r == 16 ? fused_dec_smem<16>(lgn, fit + 1) : fused_dec_smem<8>(lgn, fit + 1)) <= kPassSmem)
+        fit++;
+    if (fit < 4) return 0;
+    // slices of about S / 128 bytes (at least 16): enough CTAs to spread a
+    // short codeword over the SMs
+    const uint32_t want = std::max<uint32_t>(4u, ilog2(std::max<size_t>(S >> 7, 1)));
+    return std::min(fit, want);
+}
+
+cudaError_t launch_fused_decode(int r, const FieldTables &t, uint32_t lgn, uint8_t *shards, size_t S,
+                                const uint16_t *pre, const uint16_t *post, uint32_t lg_cw, cudaStream_t s,
+                                uint64_t *launches)
+{
+    const FusedDecArgs a{shards, S, lgn, t.rec, t.brec, t.binvrec, pre, post};
+    const dim3 grid((unsigned)((S + (1ull << lg_cw) - 1) >> lg_cw));
+    cudaError_t e;
+    if (r == 8)
+        e = launch_pdl(k_fused_dec<8>, grid, dim3(kPassThreads), fused_dec_smem<8>(lgn, lg_cw), s, a, lg_cw);
+    else
+        e = launch_pdl(k_fused_dec<16>, grid, dim3(kPassThreads), fused_dec_smem<16>(lgn, lg_cw), s, a, lg_cw);
+    *launches += 1;
+    return e;
+}
+
+uint32_t fused_enc_lg_cw(int r, uint32_t lgk, size_t S)
+{
+    if (lgk < 1 || lgk > 8) return 0;
+    uint32_t fit = 3;
+    while (fit < 12 && (1ull << (fit + 1)) < 2 * S &&
+           (r == 16 ? fused_enc_smem<16>(lgk, fit + 1) : fused_enc_smem<8>(lgk, fit + 1)) <= kPassSmem)
+        fit++;
+    if (fit < 4) return 0;
+    const uint32_t want = std::max<uint32_t>(4u, ilog2(std::max<size_t>(S >> 7, 1)));
+    return std::min(fit, want);
+}
+
+cudaError_t launch_fused_encode(int r, const FieldTables &t, uint32_t lgk, uint32_t ncos, uint8_t *shards, size_t S,
+                                uint32_t lg_cw, cudaStream_t s, uint64_t *launches)
+{
+    const FusedEncArgs a{shards, S, lgk, ncos, t.rec};
+    const dim3 grid((unsigned)((S + (1ull << lg_cw) - 1) >> lg_cw));
+    cudaError_t e;
+    if (r == 8)
+        e = launch_pdl(k_fused_enc<8>, grid, dim3(kPassThreads), fused_enc_smem<8>(lgk, lg_cw), s, a, lg_cw);
+    else
+        e = launch_pdl(k_fused_enc<16>, grid, dim3(kPassThreads), fused_enc_smem<16>(lgk, lg_cw), s, a, lg_cw);
+    *launches += 1;
+    return e;
 }
 
 cudaError_t launch_rowscale(int r, uint8_t *dst, const uint8_t *src, size_t S, uint32_t rows,

@@ -451,8 +451,16 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
         PROF(LCH_KIND_LOCATOR, 0,
              launch_locator(field, t, lgn, bits, ctx->fl[field == LCH_GF16][lgn], work, wpre, wpost, s, &ctx->launches));
     }
-    // Step 2: Phi = F * Pi, zero on erased rows (eq. hatF(l)).
     const uint64_t cols = S / (field / 8);
+    if (const uint32_t lg_cw = fused_dec_lg_cw(field, lgn, S)) {
+        // Steps 2-6 in one launch: every transform fits one tile.
+        const uint64_t m0 = (uint64_t)n / 2 * lgn - (n - 1);
+        PROFM(LCH_KIND_PASS, (uint64_t)n * S, (uint64_t)(n - ne + 2 * m0 + 2 * n + ne) * cols,
+              launch_fused_decode(field, ctx->tab[field == LCH_GF16], lgn, shards, S, pre, post, lg_cw, s,
+                                  &ctx->launches));
+        return LCH_OK;
+    }
+    // Step 2: Phi = F * Pi, zero on erased rows (eq. hatF(l)).
     PROFM(LCH_KIND_ROWSCALE, (uint64_t)(n - ne) * S + (uint64_t)n * S, (uint64_t)(n - ne) * cols,
           launch_rowscale(field, phi, shards, S, n, pre, 0, s, &ctx->launches));
     // Step 3: coefficients of hatF.
@@ -489,6 +497,16 @@ int encode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
         CU(launch_broadcast(shards + S, shards, S, n - 1, s, &ctx->launches), "broadcast");
         return LCH_OK;
     }
+    const uint32_t lgk = lg2(k);
+    const uint64_t cols = S / (field / 8);
+    if (const uint32_t lg_cw = fused_enc_lg_cw(field, lgk, S)) {
+        // the whole of Algorithm 1 in one launch: Psi_k fits one tile
+        const uint64_t m = (uint64_t)k / 2 * lgk;
+        PROFM(LCH_KIND_PASS, (uint64_t)n * S, (m - (k - 1) + (uint64_t)(n / k - 1) * m) * cols,
+              launch_fused_encode(field, ctx->tab[field == LCH_GF16], lgk, n / k - 1, shards, S, lg_cw, s,
+                                  &ctx->launches));
+        return LCH_OK;
+    }
     rc = ensure_scratch(ctx, (size_t)k * S);
     if (rc) return rc;
     uint8_t *mbar = ctx->scratch;
@@ -499,10 +517,8 @@ int encode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
     // cosets at once: the levels of Psi_k with shift ik are levels 0..lg k-1 of
     // an n-point transform with shift 0 on rows ik.., and every coset starts
     // from bar M_k (source rows masked with k - 1).
-    const uint32_t lgk = lg2(k);
     uint32_t a, b, lg[2];
     pass_plan(ctx, field, lgk, S, &a, &b, lg);
-    const uint64_t cols = S / (field / 8);
     auto coset_pass = [&](const uint8_t *src, uint32_t mask, uint32_t L0, uint32_t nlev, uint32_t lg_cw) -> int {
         PassArgs p;
         p.src = src;

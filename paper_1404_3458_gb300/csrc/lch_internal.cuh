@@ -211,6 +211,20 @@ struct DerivArgs {
 };
 cudaError_t launch_deriv(int r, int mode, const DerivArgs &a, cudaStream_t s, uint64_t *launches);
 
+// The decode of Algorithm 2 after the locator, as one launch, for lg n <= 8:
+// fused_dec_lg_cw gives its column-slice width (log2 bytes), 0 when the
+// codeword does not fit the fused form.  pre = Pi off E (0 on E), post =
+// 1/Pi' on E (0 off E); only the erased rows of shards are written.
+uint32_t fused_dec_lg_cw(int r, uint32_t lgn, size_t S);
+// Algorithm 1 as one launch for lg k <= 8 (k a power of two, ncos = n/k - 1
+// cosets written after the message rows); fused_enc_lg_cw as above.
+uint32_t fused_enc_lg_cw(int r, uint32_t lgk, size_t S);
+cudaError_t launch_fused_encode(int r, const FieldTables &t, uint32_t lgk, uint32_t ncos, uint8_t *shards, size_t S,
+                                uint32_t lg_cw, cudaStream_t s, uint64_t *launches);
+cudaError_t launch_fused_decode(int r, const FieldTables &t, uint32_t lgn, uint8_t *shards, size_t S,
+                                const uint16_t *pre, const uint16_t *post, uint32_t lg_cw, cudaStream_t s,
+                                uint64_t *launches);
+
 // c = c (.) t elementwise over `bytes` bytes (Sec. VI.A pointwise product).
 cudaError_t launch_pointwise(int r, uint8_t *c, const uint8_t *t, size_t bytes, const FieldTables &tab,
                              cudaStream_t s, uint64_t *launches);

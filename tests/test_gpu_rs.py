@@ -74,6 +74,21 @@ def test_exhaustive_8_4_all_patterns(ctx):
     assert count == 163
 
 
+@pytest.mark.parametrize("r,n,k,S", [(16, 2, 1, 32), (8, 4, 2, 16), (16, 4, 1, 48), (16, 8, 6, 4112)])
+def test_tiny_codes_all_patterns(ctx, r, n, k, S):
+    """Codes of 2 to 8 rows: every erasure pattern the code can repair, against
+    the oracle's encode (the whole decode runs as one fused launch here)."""
+    host = message(n, k, S, seed=n + k + S)
+    cw = gpu_encode(ctx, r, n, k, host)
+    cols = elem_cols(S, r, 8, seed=n)
+    assert np.array_equal(elems(cw, r)[:, cols], O.rs_encode(r, n, k, elems(host, r, cols)))
+    for e in range(n - k + 1):
+        for erased in itertools.combinations(range(n), e):
+            mask = np.zeros(n, dtype=np.uint8)
+            mask[list(erased)] = 1
+            assert np.array_equal(gpu_decode(ctx, r, n, k, cw, mask), cw), erased
+
+
 @pytest.mark.parametrize("r,n,k,S,e", [(8, 32, 16, 1024, 16), (8, 32, 16, 1024, 5), (8, 256, 128, 48, 128),
                                        (16, 64, 32, 2064, 32), (16, 1024, 512, 32, 512), (16, 8192, 4096, 16, 4000),
                                        (8, 64, 48, 80, 16), (16, 128, 96, 64, 1), (16, 4096, 2048, 48, 2048)])
