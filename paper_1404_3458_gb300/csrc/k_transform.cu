@@ -17,8 +17,10 @@
 // Kernels: k_pass_p / k_pass (transform passes, persistent and not), k_deriv_p
 // / k_deriv (formal derivative), k_rowscale (per-row constants), k_superset
 // (neighbour sums for the allocation-free derivative), k_batch (persistent
-// task queue over many codewords), k_pointwise (product of two vectors), and
-// small helpers (broadcast, row gather/scatter, fill).
+// task queue over many codewords), k_fused_enc / k_fused_dec (the whole of
+// Algorithm 1 or 2 in one launch when the transforms fit one tile),
+// k_pointwise (product of two vectors), and small helpers (broadcast, row
+// gather/scatter, fill).
 #include <algorithm>
 
 #include "lch_internal.cuh"
