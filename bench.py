@@ -540,19 +540,17 @@ def run_small_latency(ctx, torch, rank, warmup=10, reps=200):
 def run_e2e(ctx, torch, host, mask, w, args):
     """End to end through the library's Python API with host buffers.  Every
     step copies the message in from pinned host memory, encodes and copies the
-    parity out; then it copies in the surviving shards (packed, with their
-    row indices), scatters them into a codeword buffer (lch_rows_scatter),
-    decodes, gathers the recovered rows (lch_rows_gather) and copies them out.
-    Steps are pipelined over NB buffer sets and three streams (host-to-device
-    copies, compute, device-to-host copies), so one step's copies overlap the
-    neighbouring steps' kernels; each buffer is reused only after its last
-    copy out.  The last step's outputs are checked against the true codeword."""
-    from paper_1404_3458_gb300 import lch
-
+    parity out; then it copies in the surviving shards (packed, in row order),
+    decodes them with rs_decode_packed, which writes the recovered shards
+    packed in row order, and copies those out.  Steps are pipelined over NB
+    buffer sets and three streams (host-to-device copies, compute,
+    device-to-host copies), so one step's copies overlap the neighbouring
+    steps' kernels; each buffer is reused only after its last copy out.  The
+    last step's outputs are checked against the true codeword."""
     r, n, k, S = w.field, w.n, w.k, w.shard_bytes
     NB = 2
-    erased = np.nonzero(mask)[0].astype(np.int32)
-    surv = np.nonzero(mask == 0)[0].astype(np.int32)
+    erased = np.nonzero(mask)[0]
+    surv = np.nonzero(mask == 0)[0]
     ne, ns = erased.size, surv.size
     msg = torch.from_numpy(host[:k]).pin_memory()
     ref = torch.from_numpy(host).cuda()
@@ -560,14 +558,11 @@ def run_e2e(ctx, torch, host, mask, w, args):
     truth = ref.cpu()
     del ref
     surv_host = truth[torch.from_numpy(surv).long()].contiguous().pin_memory()     # the received shards
-    idx_host = torch.from_numpy(np.concatenate([surv, erased])).pin_memory()      # survivors, then erased rows
     parity_out = [torch.empty((n - k, S), dtype=torch.uint8).pin_memory() for _ in range(NB)]
     rec_out = [torch.empty((ne, S), dtype=torch.uint8).pin_memory() for _ in range(NB)]
     enc = [torch.empty((n, S), dtype=torch.uint8, device="cuda") for _ in range(NB)]
-    dec = [torch.empty((n, S), dtype=torch.uint8, device="cuda") for _ in range(NB)]
     pin_dev = [torch.empty((ns, S), dtype=torch.uint8, device="cuda") for _ in range(NB)]
     pout_dev = [torch.empty((ne, S), dtype=torch.uint8, device="cuda") for _ in range(NB)]
-    idx_dev = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(NB)]
     h2d, comp, d2h = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     freed_e, freed_d = [None] * NB, [None] * NB  # slot's last copy out has finished
 
@@ -582,15 +577,12 @@ def run_e2e(ctx, torch, host, mask, w, args):
             if freed_d[b] is not None:
                 h2d.wait_event(freed_d[b])
             pin_dev[b].copy_(surv_host, non_blocking=True)     # surviving shards in
-            idx_dev[b].copy_(idx_host, non_blocking=True)      # their row indices (and the erased ones)
             ev[1].record(h2d)
         comp.wait_event(ev[0])
         ctx.rs_encode(n, k, r, enc[b], stream=comp)
         ev[2].record(comp)
         comp.wait_event(ev[1])
-        lch.rows_scatter(pin_dev[b], dec[b], idx_dev[b][:ns], stream=comp)
-        ctx.rs_decode(n, k, r, dec[b], mask, stream=comp)
-        lch.rows_gather(dec[b], pout_dev[b], idx_dev[b][ns:], stream=comp)
+        ctx.rs_decode_packed(n, k, r, pin_dev[b], pout_dev[b], mask, stream=comp)
         ev[3].record(comp)
         with torch.cuda.stream(d2h):
             d2h.wait_event(ev[2])
@@ -619,9 +611,10 @@ def run_e2e(ctx, torch, host, mask, w, args):
     ok = bool(torch.equal(rec_out[last], truth[torch.from_numpy(erased).long()])) and \
         bool(torch.equal(parity_out[last], truth[k:]))
     return {"value": round((k + ne) * S / (ms / 1e3) / 1e9, 3), "unit": UNIT,
-            "h2d_bytes_per_step": (k + ns) * S + 4 * n, "d2h_bytes_per_step": (n - k + ne) * S,
+            "h2d_bytes_per_step": (k + ns) * S, "d2h_bytes_per_step": (n - k + ne) * S,
             "ms_per_step": round(ms, 4), "pipelined": f"{NB} buffer sets, 3 streams",
-            "received": "surviving shards only (packed, scattered on the device)", "verified": ok}
+            "received": "surviving shards only (packed); recovered shards packed (rs_decode_packed)",
+            "verified": ok}
 
 
 # --------------------------------------------------------------------------- CPU oracle

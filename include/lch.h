@@ -140,6 +140,18 @@ LCH_API int rs_encode(lch_ctx *ctx, uint32_t n, uint32_t k, int field, void *sha
 LCH_API int rs_decode(lch_ctx *ctx, uint32_t n, uint32_t k, int field, void *shards, size_t shard_bytes,
                       const uint8_t *erasure_mask, void *stream);
 
+/* Erasure decoding from the received shards alone (Algorithm 2, as
+ * rs_decode), without assembling the codeword: `received` (device) holds the
+ * n - |E| surviving shards packed in increasing row order, and `recovered`
+ * (device, |E| shard_bytes bytes) receives the erased shards packed in
+ * increasing row order.  erasure_mask as in rs_decode; both pointers must be
+ * 16-byte aligned.  With no erasures the call returns LCH_OK and touches
+ * nothing; with more than n - k it returns LCH_ETOOMANY.  The received
+ * shards are only read.  Uses context scratch of about 2 n shard_bytes
+ * bytes. */
+LCH_API int rs_decode_packed(lch_ctx *ctx, uint32_t n, uint32_t k, int field, const void *received,
+                             void *recovered, size_t shard_bytes, const uint8_t *erasure_mask, void *stream);
+
 /* ---- Batches: many independent codewords in one persistent launch -------
  * (Beyond the paper, which treats one codeword at a time: every stage of
  * Algorithms 1 and 2 is the same per codeword, so the stages of thousands of

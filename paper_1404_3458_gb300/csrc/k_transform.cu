@@ -997,7 +997,7 @@ template <int R, uint32_t Q = 0> struct RowsScale {
 template <int R>
 __global__ void __launch_bounds__(kThreads)
     k_rowscale(uint8_t *dst, const uint8_t *src, size_t S, uint32_t rows, const uint16_t *__restrict__ coef,
-               int skip_zero)
+               int skip_zero, RowPack pk)
 {
     __shared__ __align__(128) uint8_t T[kRowsPerCta * FT<R>::rec_bytes];
     pdl_trigger();
@@ -1008,14 +1008,29 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (uint32_t q = 0; q < kRowsPerCta; q++) k[q] = r0 + q < rows ? coef[r0 + q] : 0u;
     const size_t vpr = S / 16;
-    const uint4 *s4 = reinterpret_cast<const uint4 *>(src) + (size_t)r0 * vpr;
-    uint4 *d4 = reinterpret_cast<uint4 *>(dst) + (size_t)r0 * vpr;
+    // row q's place in src and in dst: row r0 + q, or its rank among the
+    // surviving / erased rows when that side is packed
+    uint32_t srow[kRowsPerCta], drow[kRowsPerCta];
+#pragma unroll
+    for (uint32_t q = 0; q < kRowsPerCta; q++) {
+        const uint32_t row = r0 + q;
+        uint32_t ne = 0;
+        if (pk.mode && row < rows) {
+            const uint32_t w = row >> 5;
+            ne = pk.rank[w] + __popc(pk.bits[w] & ((1u << (row & 31u)) - 1u));
+        }
+        srow[q] = (pk.mode & 1) ? row - ne : row;
+        drow[q] = (pk.mode & 2) ? ne : row;
+    }
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
     // the first slice's rows are read before the tables are built, so the
     // loads are in flight meanwhile
     uint4 x[kRowsPerCta];
     if (threadIdx.x < vpr) {
 #pragma unroll
-        for (uint32_t q = 0; q < kRowsPerCta; q++) x[q] = k[q] ? s4[q * vpr + threadIdx.x] : make_uint4(0, 0, 0, 0);
+        for (uint32_t q = 0; q < kRowsPerCta; q++)
+            x[q] = k[q] ? s4[srow[q] * vpr + threadIdx.x] : make_uint4(0, 0, 0, 0);
     }
     for (uint32_t v = threadIdx.x; v < kRowsPerCta * cpr; v += blockDim.x) {
         const uint32_t q = v / cpr, c = v - q * cpr;
@@ -1027,12 +1042,12 @@ __global__ void __launch_bounds__(kThreads)
     for (size_t i = threadIdx.x; i < vpr; i += blockDim.x) {
         if (i != threadIdx.x) {
 #pragma unroll
-            for (uint32_t q = 0; q < kRowsPerCta; q++) x[q] = k[q] ? s4[q * vpr + i] : make_uint4(0, 0, 0, 0);
+            for (uint32_t q = 0; q < kRowsPerCta; q++) x[q] = k[q] ? s4[srow[q] * vpr + i] : make_uint4(0, 0, 0, 0);
         }
         RowsScale<R>::run(x, k, t);
 #pragma unroll
         for (uint32_t q = 0; q < kRowsPerCta; q++)
-            if (r0 + q < rows && (k[q] || !skip_zero)) d4[q * vpr + i] = x[q];
+            if (r0 + q < rows && (k[q] || !skip_zero)) d4[drow[q] * vpr + i] = x[q];
     }
 }
 
@@ -1803,16 +1818,66 @@ cudaError_t launch_fused_encode(int r, const FieldTables &t, uint32_t lgk, uint3
     return e;
 }
 
+// Erased-row ranks for packed row addressing: out_bits[w] = mask word w,
+// out_rank[w] = erased rows before row 32 w (one CTA; nwords <= 2048).
+__global__ void __launch_bounds__(1024) k_rank(MaskBits bits, uint32_t nwords, uint32_t *out_bits, uint32_t *out_rank)
+{
+    __shared__ uint32_t part[32];
+    pdl_trigger();
+    pdl_wait(); // a predecessor may still read the previous ranks
+    const uint32_t t = threadIdx.x, lane = t & 31u, warp = t >> 5;
+    const uint32_t w0 = 2 * t, w1 = 2 * t + 1;
+    const uint32_t b0 = w0 < nwords ? bits.w[w0] : 0u, b1 = w1 < nwords ? bits.w[w1] : 0u;
+    const uint32_t c = __popc(b0) + __popc(b1);
+    uint32_t incl = c; // inclusive scan within the warp
+#pragma unroll
+    for (uint32_t d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) part[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = part[lane], sc = v;
+#pragma unroll
+        for (uint32_t d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, sc, d);
+            if (lane >= d) sc += y;
+        }
+        part[lane] = sc - v; // exclusive prefix of the warps
+    }
+    __syncthreads();
+    const uint32_t before = part[warp] + incl - c;
+    if (w0 < nwords) {
+        out_bits[w0] = b0;
+        out_rank[w0] = before;
+    }
+    if (w1 < nwords) {
+        out_bits[w1] = b1;
+        out_rank[w1] = before + __popc(b0);
+    }
+}
+
+cudaError_t launch_rank(const MaskBits &bits, uint32_t n, uint32_t *out_bits, uint32_t *out_rank, cudaStream_t s,
+                        uint64_t *launches)
+{
+    const uint32_t nwords = (n + 31) / 32;
+    cudaError_t e = launch_pdl(k_rank, dim3(1), dim3(1024), 0, s, bits, nwords, out_bits, out_rank);
+    *launches += 1;
+    return e;
+}
+
 cudaError_t launch_rowscale(int r, uint8_t *dst, const uint8_t *src, size_t S, uint32_t rows,
-                            const uint16_t *coef, int skip_zero, cudaStream_t s, uint64_t *launches)
+                            const uint16_t *coef, int skip_zero, cudaStream_t s, uint64_t *launches,
+                            const RowPack &pk)
 {
     if (rows == 0) return cudaSuccess;
     const uint32_t ctas = (rows + kRowsPerCta - 1) / kRowsPerCta;
     cudaError_t e;
     if (r == 8)
-        e = launch_pdl(k_rowscale<8>, dim3(ctas), dim3(kThreads), 0, s, dst, src, S, rows, coef, skip_zero);
+        e = launch_pdl(k_rowscale<8>, dim3(ctas), dim3(kThreads), 0, s, dst, src, S, rows, coef, skip_zero, pk);
     else
-        e = launch_pdl(k_rowscale<16>, dim3(ctas), dim3(kThreads), 0, s, dst, src, S, rows, coef, skip_zero);
+        e = launch_pdl(k_rowscale<16>, dim3(ctas), dim3(kThreads), 0, s, dst, src, S, rows, coef, skip_zero, pk);
     if (e != cudaSuccess) return e;
     *launches += 1;
     return cudaGetLastError();

@@ -412,9 +412,14 @@ int ensure_shortened(lch_ctx *ctx, int field, uint32_t n, uint32_t k, cudaStream
 
 // Algorithm 2 on the rows flagged in `mask`.  `loc` (optional) holds Pi and
 // 1/Pi' for exactly this erasure set (2n uint16); the locator is then skipped.
+// In place on the n-row codeword `shards`; or, when `received` is given, from
+// the surviving rows packed in row order there, writing the erased rows
+// packed in row order to `recovered` (shards unused).
 int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards, size_t S, const uint8_t *mask,
-                cudaStream_t s, const uint16_t *loc = nullptr)
+                cudaStream_t s, const uint16_t *loc = nullptr, const uint8_t *received = nullptr,
+                uint8_t *recovered = nullptr)
 {
+    const bool packed = received != nullptr;
     const uint32_t lgn = lg2(n);
     MaskBits bits;
     memset(&bits, 0, sizeof(bits));
@@ -432,7 +437,8 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
     const size_t off_phi2 = align_up(body), off_pre = off_phi2 + align_up(body);
     const size_t off_post = off_pre + align_up(sizeof(uint16_t) * n);
     const size_t off_work = off_post + align_up(sizeof(uint16_t) * n);
-    rc = ensure_scratch(ctx, off_work + align_up(sizeof(uint32_t) * n));
+    const size_t nwords = (n + 31) / 32, off_rank = off_work + align_up(sizeof(uint32_t) * n);
+    rc = ensure_scratch(ctx, off_rank + 2 * align_up(sizeof(uint32_t) * nwords));
     if (rc) return rc;
     uint8_t *phi = ctx->scratch, *phi2 = ctx->scratch + off_phi2;
     const uint16_t *pre = reinterpret_cast<uint16_t *>(ctx->scratch + off_pre);
@@ -452,7 +458,7 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
              launch_locator(field, t, lgn, bits, ctx->fl[field == LCH_GF16][lgn], work, wpre, wpost, s, &ctx->launches));
     }
     const uint64_t cols = S / (field / 8);
-    if (const uint32_t lg_cw = fused_dec_lg_cw(field, lgn, S)) {
+    if (const uint32_t lg_cw = packed ? 0 : fused_dec_lg_cw(field, lgn, S)) {
         // Steps 2-6 in one launch: every transform fits one tile.
         const uint64_t m0 = (uint64_t)n / 2 * lgn - (n - 1);
         PROFM(LCH_KIND_PASS, (uint64_t)n * S, (uint64_t)(n - ne + 2 * m0 + 2 * n + ne) * cols,
@@ -460,9 +466,18 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
                                   &ctx->launches));
         return LCH_OK;
     }
+    RowPack pk;
+    if (packed) {
+        pk.bits = reinterpret_cast<uint32_t *>(ctx->scratch + off_rank);
+        pk.rank = pk.bits + align_up(sizeof(uint32_t) * nwords) / sizeof(uint32_t);
+        PROF(LCH_KIND_LOCATOR, 0,
+             launch_rank(bits, n, const_cast<uint32_t *>(pk.bits), const_cast<uint32_t *>(pk.rank), s,
+                         &ctx->launches));
+    }
     // Step 2: Phi = F * Pi, zero on erased rows (eq. hatF(l)).
+    pk.mode = packed ? 1 : 0;
     PROFM(LCH_KIND_ROWSCALE, (uint64_t)(n - ne) * S + (uint64_t)n * S, (uint64_t)(n - ne) * cols,
-          launch_rowscale(field, phi, shards, S, n, pre, 0, s, &ctx->launches));
+          launch_rowscale(field, phi, packed ? received : shards, S, n, pre, 0, s, &ctx->launches, pk));
     // Step 3: coefficients of hatF.
     rc = transform(ctx, field, n, 0, 1, phi, phi, S, s);
     if (rc) return rc;
@@ -474,7 +489,8 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
     if (rc) return rc;
     // Step 6: F(j) = hatF'(j) / Pi'(j), written to the erased rows only.
     PROFM(LCH_KIND_ROWSCALE, 2ull * ne * S, (uint64_t)ne * cols,
-          launch_rowscale(field, shards, phi2, S, n, post, 1, s, &ctx->launches));
+          launch_rowscale(field, packed ? recovered : shards, phi2, S, n, post, 1, s, &ctx->launches,
+                          RowPack{packed ? 2 : 0, pk.bits, pk.rank}));
     return LCH_OK;
 }
 
@@ -1073,6 +1089,25 @@ LCH_API int rs_decode(lch_ctx *ctx, uint32_t n, uint32_t k, int field, void *sha
     return decode_impl(ctx, n, k, field, (uint8_t *)shards, shard_bytes, erasure_mask, (cudaStream_t)stream);
 }
 
+
+LCH_API int rs_decode_packed(lch_ctx *ctx, uint32_t n, uint32_t k, int field, const void *received,
+                             void *recovered, size_t shard_bytes, const uint8_t *erasure_mask, void *stream)
+{
+    int rc;
+    if ((rc = check_field(field)) || (rc = check_len("n", n, field))) return rc;
+    if (k == 0 || k > n) return fail(LCH_EINVAL, "k must satisfy 1 <= k <= n, got k=%u n=%u", k, n);
+    if (!erasure_mask) return fail(LCH_EINVAL, "erasure_mask is NULL");
+    uint32_t ne = 0;
+    for (uint32_t j = 0; j < n; j++) ne += erasure_mask[j] != 0;
+    if (ne == 0) return LCH_OK;
+    if (ne < n && (rc = check_buffer(received, n - ne, shard_bytes))) return rc;
+    if ((rc = check_buffer(recovered, ne, shard_bytes))) return rc;
+    if (!ctx) return fail(LCH_EINVAL, "ctx is NULL");
+    DeviceScope ds(ctx->device);
+    if (!ds.ok) return fail(LCH_ECUDA, "cannot select device %d", ctx->device);
+    return decode_impl(ctx, n, k, field, nullptr, shard_bytes, erasure_mask, (cudaStream_t)stream, nullptr,
+                       (const uint8_t *)received, (uint8_t *)recovered);
+}
 
 LCH_API int lch_batch_create(lch_ctx *ctx, int op, const lch_codeword *cws, uint32_t count, lch_batch **out)
 {

@@ -75,6 +75,7 @@ def load() -> ctypes.CDLL:
         "lch_derivative": (i, [vp, i, u32, vp, sz, vp]),
         "rs_encode": (i, [vp, u32, u32, i, vp, sz, vp]),
         "rs_decode": (i, [vp, u32, u32, i, vp, sz, vp, vp]),
+        "rs_decode_packed": (i, [vp, u32, u32, i, vp, vp, sz, vp, vp]),
         "lch_strerror": (ctypes.c_char_p, [i]),
         "lch_last_error": (ctypes.c_char_p, []),
         "lch_launch_count": (ctypes.c_uint64, [vp]),
@@ -351,3 +352,18 @@ class Context:
             raise ValueError(f"erasure mask must have n={n} entries")
         _check(load().rs_decode(self._h, n, k, field, p, S, m.ctypes.data_as(ctypes.c_void_p),
                                 _stream_handle(stream)))
+
+    # Algorithm 2 from the received shards alone: `received` holds the
+    # n - |E| surviving shards in row order, `recovered` gets the |E| erased
+    # ones in row order; the codeword is never assembled.
+    def rs_decode_packed(self, n: int, k: int, field: int, received, recovered, erasure_mask, stream=None):
+        m = np.ascontiguousarray(np.asarray(erasure_mask, dtype=np.uint8).reshape(-1))
+        if m.size != n:
+            raise ValueError(f"erasure mask must have n={n} entries")
+        ne = int(np.count_nonzero(m))
+        pr, S = _buf(received, n - ne)
+        po, S2 = _buf(recovered, ne)
+        if S2 != S:
+            raise ValueError("received and recovered shards differ in size")
+        _check(load().rs_decode_packed(self._h, n, k, field, pr, po, S, m.ctypes.data_as(ctypes.c_void_p),
+                                       _stream_handle(stream)))

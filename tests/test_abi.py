@@ -49,6 +49,22 @@ def test_encode_argument_checks(L, args, needle):
     assert needle in lch.last_error()
 
 
+def test_decode_packed_argument_checks(L):
+    mask = (ctypes.c_uint8 * 32)()
+    mask[3] = 1
+    assert L.rs_decode_packed(None, 32, 16, 8, FAKE, FAKE, 1024, None, None) == lch.LCH_EINVAL
+    assert "erasure_mask is NULL" in lch.last_error()
+    assert L.rs_decode_packed(None, 32, 16, 8, FAKE, None, 1024, mask, None) == lch.LCH_EINVAL
+    assert "NULL" in lch.last_error()
+    assert L.rs_decode_packed(None, 32, 16, 8, MISALIGNED, FAKE, 1024, mask, None) == lch.LCH_EINVAL
+    assert "16-byte aligned" in lch.last_error()
+    assert L.rs_decode_packed(None, 32, 16, 8, FAKE, FAKE, 1000, mask, None) == lch.LCH_EINVAL
+    assert L.rs_decode_packed(None, 32, 16, 8, FAKE, FAKE, 1024, mask, None) == lch.LCH_EINVAL
+    assert "ctx is NULL" in lch.last_error()
+    # no erasures: nothing to do, whatever the buffers
+    assert L.rs_decode_packed(None, 32, 16, 8, None, None, 1024, (ctypes.c_uint8 * 32)(), None) == lch.LCH_OK
+
+
 def test_decode_and_transform_argument_checks(L):
     mask = (ctypes.c_uint8 * 32)()
     assert L.rs_decode(None, 32, 16, 8, FAKE, 1024, None, None) == lch.LCH_EINVAL

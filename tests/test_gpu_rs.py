@@ -193,6 +193,53 @@ def test_encode_many_cosets(ctx, r, n, k, S):
     assert np.array_equal(elems(got, r)[rows][:, cols], expect[rows])
 
 
+@pytest.mark.parametrize("r,n,k,S,kind", [(8, 32, 16, 1024, "random"), (8, 8, 4, 16, "random"),
+                                          (16, 256, 64, 208, "random"), (16, 1024, 512, 48, "burst"),
+                                          (16, 4096, 3072, 64, "random"), (16, 65536, 32768, 32, "random"),
+                                          (16, 65536, 32768, 16, "burst"), (8, 64, 48, 80, "random")])
+def test_decode_packed_matches_in_place(ctx, r, n, k, S, kind):
+    """rs_decode_packed, from the surviving shards alone, recovers exactly the
+    erased rows that rs_decode restores in place (and the true codeword)."""
+    import torch
+
+    cw = gpu_encode(ctx, r, n, k, message(n, k, S, seed=n + S))
+    e = n - k
+    mask = WL.erasure_mask(n, e, seed=n + 7) if kind == "random" else WL.burst_mask(n, e, (n - e) // 3)
+    erased = np.nonzero(mask)[0]
+    surv = np.nonzero(mask == 0)[0]
+    received = to_dev(np.ascontiguousarray(cw[surv]))
+    recovered = torch.full((len(erased), S), 0xC3, dtype=torch.uint8, device="cuda")
+    ctx.rs_decode_packed(n, k, r, received, recovered, mask)
+    assert np.array_equal(recovered.cpu().numpy(), cw[erased])
+    assert np.array_equal(received.cpu().numpy(), cw[surv])  # only read
+    assert np.array_equal(gpu_decode(ctx, r, n, k, cw, mask)[erased], cw[erased])
+
+
+def test_decode_packed_edge_cases(ctx):
+    import torch
+
+    r, n, k, S = 16, 64, 32, 64
+    cw = gpu_encode(ctx, r, n, k, message(n, k, S, seed=11))
+    # no erasures: nothing to do
+    empty = torch.empty((0, S), dtype=torch.uint8, device="cuda")
+    ctx.rs_decode_packed(n, k, r, to_dev(cw), empty, np.zeros(n, np.uint8))
+    # more than n - k erasures: refused, nothing written
+    mask = np.zeros(n, np.uint8)
+    mask[: n - k + 1] = 1
+    out = torch.zeros((n - k + 1, S), dtype=torch.uint8, device="cuda")
+    with pytest.raises(lch.LchError) as ei:
+        ctx.rs_decode_packed(n, k, r, to_dev(cw[n - k + 1:]), out, mask)
+    assert ei.value.status == lch.LCH_ETOOMANY
+    assert not out.any()
+    # a single erasure, in each position of a short code
+    for j in (0, 31, 63):
+        mask = np.zeros(n, np.uint8)
+        mask[j] = 1
+        out = torch.empty((1, S), dtype=torch.uint8, device="cuda")
+        ctx.rs_decode_packed(n, k, r, to_dev(np.delete(cw, j, axis=0)), out, mask)
+        assert np.array_equal(out.cpu().numpy()[0], cw[j])
+
+
 def test_rows_gather_scatter_round_trip():
     """lch_rows_scatter / lch_rows_gather move whole rows by a device index
     array: scattering the survivors of a codeword into a fresh buffer and
