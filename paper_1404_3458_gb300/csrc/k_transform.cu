@@ -1004,24 +1004,24 @@ __global__ void __launch_bounds__(kThreads)
     pdl_wait(); // coef and src come from predecessors
     const uint32_t r0 = blockIdx.x * kRowsPerCta;
     constexpr uint32_t cpr = FT<R>::rec_bytes / 16;
-    uint32_t k[kRowsPerCta];
-#pragma unroll
-    for (uint32_t q = 0; q < kRowsPerCta; q++) k[q] = r0 + q < rows ? coef[r0 + q] : 0u;
-    const size_t vpr = S / 16;
-    // row q's place in src and in dst: row r0 + q, or its rank among the
-    // surviving / erased rows when that side is packed
-    uint32_t srow[kRowsPerCta], drow[kRowsPerCta];
+    // row q is row r0 + q, or (mode 4) list entry r0 + q; its place in src
+    // and in dst is the row itself, or its rank among the surviving / erased
+    // rows when that side is packed
+    uint32_t k[kRowsPerCta], srow[kRowsPerCta], drow[kRowsPerCta];
 #pragma unroll
     for (uint32_t q = 0; q < kRowsPerCta; q++) {
-        const uint32_t row = r0 + q;
-        uint32_t ne = 0;
-        if (pk.mode && row < rows) {
+        const bool in = r0 + q < rows;
+        const uint32_t row = (pk.mode & 4) ? (in ? pk.list[r0 + q] : 0u) : r0 + q;
+        k[q] = in ? coef[row] : 0u;
+        uint32_t ne = r0 + q; // list entries are erased rows in increasing order
+        if ((pk.mode & 3) && !(pk.mode & 4) && in) {
             const uint32_t w = row >> 5;
             ne = pk.rank[w] + __popc(pk.bits[w] & ((1u << (row & 31u)) - 1u));
         }
         srow[q] = (pk.mode & 1) ? row - ne : row;
         drow[q] = (pk.mode & 2) ? ne : row;
     }
+    const size_t vpr = S / 16;
     const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
     uint4 *d4 = reinterpret_cast<uint4 *>(dst);
     // the first slice's rows are read before the tables are built, so the
@@ -1034,7 +1034,9 @@ __global__ void __launch_bounds__(kThreads)
     }
     for (uint32_t v = threadIdx.x; v < kRowsPerCta * cpr; v += blockDim.x) {
         const uint32_t q = v / cpr, c = v - q * cpr;
-        const uint32_t kq = r0 + q < rows ? coef[r0 + q] : 0u;
+        uint32_t kq = 0;
+#pragma unroll
+        for (uint32_t i = 0; i < kRowsPerCta; i++) kq = i == q ? k[i] : kq;
         *reinterpret_cast<uint4 *>(T + rec_dst<R>(kRowsPerCta, q, c)) = rec_chunk<R>(kq, c);
     }
     __syncthreads();
@@ -1819,10 +1821,13 @@ cudaError_t launch_fused_encode(int r, const FieldTables &t, uint32_t lgk, uint3
 }
 
 // Erased-row ranks for packed row addressing: out_bits[w] = mask word w,
-// out_rank[w] = erased rows before row 32 w (one CTA; nwords <= 2048).
-__global__ void __launch_bounds__(1024) k_rank(MaskBits bits, uint32_t nwords, uint32_t *out_bits, uint32_t *out_rank)
+// out_rank[w] = erased rows before row 32 w, out_list = the erased rows in
+// increasing order (one CTA; nwords <= 2048).
+__global__ void __launch_bounds__(1024) k_rank(MaskBits bits, uint32_t nwords, uint32_t *out_bits, uint32_t *out_rank,
+                                               uint32_t *out_list)
 {
     __shared__ uint32_t part[32];
+    __shared__ uint32_t rk[kMaxN / 32];
     pdl_trigger();
     pdl_wait(); // a predecessor may still read the previous ranks
     const uint32_t t = threadIdx.x, lane = t & 31u, warp = t >> 5;
@@ -1850,19 +1855,25 @@ __global__ void __launch_bounds__(1024) k_rank(MaskBits bits, uint32_t nwords, u
     const uint32_t before = part[warp] + incl - c;
     if (w0 < nwords) {
         out_bits[w0] = b0;
-        out_rank[w0] = before;
+        out_rank[w0] = rk[w0] = before;
     }
     if (w1 < nwords) {
         out_bits[w1] = b1;
-        out_rank[w1] = before + __popc(b0);
+        out_rank[w1] = rk[w1] = before + __popc(b0);
+    }
+    __syncthreads();
+    // the list: a warp per word, lane l for row 32 w + l (coalesced stores)
+    for (uint32_t w = warp; w < nwords; w += 32) {
+        const uint32_t b = bits.w[w];
+        if ((b >> lane) & 1u) out_list[rk[w] + __popc(b & ((1u << lane) - 1u))] = 32 * w + lane;
     }
 }
 
-cudaError_t launch_rank(const MaskBits &bits, uint32_t n, uint32_t *out_bits, uint32_t *out_rank, cudaStream_t s,
-                        uint64_t *launches)
+cudaError_t launch_rank(const MaskBits &bits, uint32_t n, uint32_t *out_bits, uint32_t *out_rank, uint32_t *out_list,
+                        cudaStream_t s, uint64_t *launches)
 {
     const uint32_t nwords = (n + 31) / 32;
-    cudaError_t e = launch_pdl(k_rank, dim3(1), dim3(1024), 0, s, bits, nwords, out_bits, out_rank);
+    cudaError_t e = launch_pdl(k_rank, dim3(1), dim3(1024), 0, s, bits, nwords, out_bits, out_rank, out_list);
     *launches += 1;
     return e;
 }

@@ -438,7 +438,8 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
     const size_t off_post = off_pre + align_up(sizeof(uint16_t) * n);
     const size_t off_work = off_post + align_up(sizeof(uint16_t) * n);
     const size_t nwords = (n + 31) / 32, off_rank = off_work + align_up(sizeof(uint32_t) * n);
-    rc = ensure_scratch(ctx, off_rank + 2 * align_up(sizeof(uint32_t) * nwords));
+    const size_t off_list = off_rank + 2 * align_up(sizeof(uint32_t) * nwords);
+    rc = ensure_scratch(ctx, off_list + align_up(sizeof(uint32_t) * n));
     if (rc) return rc;
     uint8_t *phi = ctx->scratch, *phi2 = ctx->scratch + off_phi2;
     const uint16_t *pre = reinterpret_cast<uint16_t *>(ctx->scratch + off_pre);
@@ -466,13 +467,16 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
                                   &ctx->launches));
         return LCH_OK;
     }
+    // the erased rows' ranks and list (row addressing of steps 2 and 6)
     RowPack pk;
-    if (packed) {
-        pk.bits = reinterpret_cast<uint32_t *>(ctx->scratch + off_rank);
-        pk.rank = pk.bits + align_up(sizeof(uint32_t) * nwords) / sizeof(uint32_t);
-        PROF(LCH_KIND_LOCATOR, 0,
-             launch_rank(bits, n, const_cast<uint32_t *>(pk.bits), const_cast<uint32_t *>(pk.rank), s,
-                         &ctx->launches));
+    {
+        uint32_t *wbits = reinterpret_cast<uint32_t *>(ctx->scratch + off_rank);
+        uint32_t *wrank = wbits + align_up(sizeof(uint32_t) * nwords) / sizeof(uint32_t);
+        uint32_t *wlist = reinterpret_cast<uint32_t *>(ctx->scratch + off_list);
+        PROF(LCH_KIND_LOCATOR, 0, launch_rank(bits, n, wbits, wrank, wlist, s, &ctx->launches));
+        pk.bits = wbits;
+        pk.rank = wrank;
+        pk.list = wlist;
     }
     // Step 2: Phi = F * Pi, zero on erased rows (eq. hatF(l)).
     pk.mode = packed ? 1 : 0;
@@ -489,8 +493,8 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
     if (rc) return rc;
     // Step 6: F(j) = hatF'(j) / Pi'(j), written to the erased rows only.
     PROFM(LCH_KIND_ROWSCALE, 2ull * ne * S, (uint64_t)ne * cols,
-          launch_rowscale(field, packed ? recovered : shards, phi2, S, n, post, 1, s, &ctx->launches,
-                          RowPack{packed ? 2 : 0, pk.bits, pk.rank}));
+          launch_rowscale(field, packed ? recovered : shards, phi2, S, ne, post, 1, s, &ctx->launches,
+                          RowPack{packed ? 6 : 4, pk.bits, pk.rank, pk.list}));
     return LCH_OK;
 }
 

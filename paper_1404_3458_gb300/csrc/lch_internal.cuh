@@ -229,13 +229,16 @@ cudaError_t launch_fused_decode(int r, const FieldTables &t, uint32_t lgn, uint8
 cudaError_t launch_pointwise(int r, uint8_t *c, const uint8_t *t, size_t bytes, const FieldTables &tab,
                              cudaStream_t s, uint64_t *launches);
 
-// Packed row addressing for the row scaling of a decode from packed shards:
-// mode bit 0, src holds only the surviving rows (in row order); bit 1, dst
-// holds only the erased rows.  bits/rank come from launch_rank.
+// Row addressing of the row scaling in a decode: mode bit 0, src holds only
+// the surviving rows (packed in row order); bit 1, dst holds only the erased
+// rows; bit 2, the `rows` rows scaled are the entries of list (the erased
+// rows in increasing order) rather than rows 0 .. rows-1.  bits/rank/list come
+// from launch_rank.
 struct RowPack {
     int mode = 0;
     const uint32_t *bits = nullptr; // erasure bitmap, one word per 32 rows
     const uint32_t *rank = nullptr; // erased rows before each word
+    const uint32_t *list = nullptr; // the erased rows, increasing
 };
 
 // dst[t] = src[t] * coef[t] for t < rows (a zero coefficient zeroes the row);
@@ -295,9 +298,10 @@ __device__ __forceinline__ void emit(uint32_t j, uint32_t c, uint32_t erased, co
 __device__ __forceinline__ uint32_t mask_bit(const MaskBits &b, uint32_t j) { return (b.w[j >> 5] >> (j & 31u)) & 1u; }
 
 // The bitmap of n rows and, per word, the erased rows before it, into device
-// arrays of ceil(n / 32) words each (for RowPack).
-cudaError_t launch_rank(const MaskBits &bits, uint32_t n, uint32_t *out_bits, uint32_t *out_rank, cudaStream_t s,
-                        uint64_t *launches);
+// arrays of ceil(n / 32) words each, and the erased rows in increasing order
+// into out_list (for RowPack).
+cudaError_t launch_rank(const MaskBits &bits, uint32_t n, uint32_t *out_bits, uint32_t *out_rank, uint32_t *out_list,
+                        cudaStream_t s, uint64_t *launches);
 
 cudaError_t launch_fwht_log_table(int r, const FieldTables &t, uint32_t lgn, uint32_t *fl,
                                   uint32_t *work, cudaStream_t s, uint64_t *launches);

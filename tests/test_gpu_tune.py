@@ -23,12 +23,13 @@ def tctx():
 
 def plans_for(r, lgh, S):
     """Hand-set plans: every split with both passes <= 8 levels, each with the
-    narrowest (16-byte) and a wide column tile."""
+    narrowest (16-byte), a 64-byte and a 256-byte column tile (from 256 bytes
+    up the persistent pass splits its CTA into two column halves)."""
     out = []
     splits = [lgh] if lgh <= 8 else [a for a in range(1, 9) if 1 <= lgh - a <= 8]
     for a in splits:
         b = lgh - a
-        for lo, hi in ((4, 4 if b else 0), (6, 6 if b else 0)):
+        for lo, hi in ((4, 4 if b else 0), (6, 6 if b else 0), (8, 8 if b else 0)):
             cap = max(4, int(np.ceil(np.log2(S))))
             out.append({"split": a, "lg_tile_low": min(lo, cap), "lg_tile_high": min(hi, cap) if b else 0})
     return out
