@@ -486,7 +486,7 @@ def run_serving(ctx, torch, args, rank):
                     for i, (r, n, k, S, e) in enumerate(specs)]
             torch.cuda.synchronize()
             if name == "served":
-                srv = SV.Server(ctx, budget, max_inflight=2, max_batch=1024, max_batch_bytes=2 * 10**9)
+                srv = SV.Server(ctx, budget, max_inflight=3, max_batch=1024, max_batch_bytes=2 * 10**9)
                 srv.prewarm([(r, n, k, S) for (r, n, k, S, e) in specs])
                 st = srv.run(reqs)
                 del srv

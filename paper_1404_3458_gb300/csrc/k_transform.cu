@@ -1822,19 +1822,34 @@ cudaError_t launch_fused_encode(int r, const FieldTables &t, uint32_t lgk, uint3
 
 // Erased-row ranks for packed row addressing: out_bits[w] = mask word w,
 // out_rank[w] = erased rows before row 32 w, out_list = the erased rows in
-// increasing order (one CTA; nwords <= 2048).
+// increasing order.  CTA b takes words [256 b, 256 b + 256): it counts the
+// erased rows of the words before its range, scans its own words and writes
+// their list entries (a warp per word, coalesced).
+constexpr uint32_t kRankWords = 256;
 __global__ void __launch_bounds__(1024) k_rank(MaskBits bits, uint32_t nwords, uint32_t *out_bits, uint32_t *out_rank,
                                                uint32_t *out_list)
 {
     __shared__ uint32_t part[32];
-    __shared__ uint32_t rk[kMaxN / 32];
+    __shared__ uint32_t rk[kRankWords];
     pdl_trigger();
     pdl_wait(); // a predecessor may still read the previous ranks
     const uint32_t t = threadIdx.x, lane = t & 31u, warp = t >> 5;
-    const uint32_t w0 = 2 * t, w1 = 2 * t + 1;
-    const uint32_t b0 = w0 < nwords ? bits.w[w0] : 0u, b1 = w1 < nwords ? bits.w[w1] : 0u;
-    const uint32_t c = __popc(b0) + __popc(b1);
-    uint32_t incl = c; // inclusive scan within the warp
+    const uint32_t w_lo = blockIdx.x * kRankWords;
+    // erased rows before this CTA's words
+    uint32_t c = 0;
+    for (uint32_t w = t; w < w_lo; w += blockDim.x) c += __popc(bits.w[w]);
+#pragma unroll
+    for (uint32_t d = 16; d; d >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, d);
+    if (lane == 0) part[warp] = c;
+    __syncthreads();
+    uint32_t base = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < 32; i++) base += part[i];
+    __syncthreads();
+    // exclusive scan of this CTA's words (threads 0 .. 255, one word each)
+    const uint32_t w = w_lo + t;
+    const uint32_t b = (t < kRankWords && w < nwords) ? bits.w[w] : 0u;
+    uint32_t incl = __popc(b);
 #pragma unroll
     for (uint32_t d = 1; d < 32; d <<= 1) {
         const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
@@ -1842,30 +1857,21 @@ __global__ void __launch_bounds__(1024) k_rank(MaskBits bits, uint32_t nwords, u
     }
     if (lane == 31) part[warp] = incl;
     __syncthreads();
-    if (warp == 0) {
-        uint32_t v = part[lane], sc = v;
-#pragma unroll
-        for (uint32_t d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, sc, d);
-            if (lane >= d) sc += y;
+    uint32_t wbefore = 0;
+    for (uint32_t i = 0; i < warp; i++) wbefore += part[i];
+    if (t < kRankWords) {
+        const uint32_t r = base + wbefore + incl - __popc(b);
+        rk[t] = r;
+        if (w < nwords) {
+            out_bits[w] = b;
+            out_rank[w] = r;
         }
-        part[lane] = sc - v; // exclusive prefix of the warps
     }
     __syncthreads();
-    const uint32_t before = part[warp] + incl - c;
-    if (w0 < nwords) {
-        out_bits[w0] = b0;
-        out_rank[w0] = rk[w0] = before;
-    }
-    if (w1 < nwords) {
-        out_bits[w1] = b1;
-        out_rank[w1] = rk[w1] = before + __popc(b0);
-    }
-    __syncthreads();
-    // the list: a warp per word, lane l for row 32 w + l (coalesced stores)
-    for (uint32_t w = warp; w < nwords; w += 32) {
-        const uint32_t b = bits.w[w];
-        if ((b >> lane) & 1u) out_list[rk[w] + __popc(b & ((1u << lane) - 1u))] = 32 * w + lane;
+    // the list: a warp per word, lane l for row 32 w + l
+    for (uint32_t i = warp; i < kRankWords && w_lo + i < nwords; i += 32) {
+        const uint32_t bw = bits.w[w_lo + i];
+        if ((bw >> lane) & 1u) out_list[rk[i] + __popc(bw & ((1u << lane) - 1u))] = 32 * (w_lo + i) + lane;
     }
 }
 
@@ -1873,7 +1879,8 @@ cudaError_t launch_rank(const MaskBits &bits, uint32_t n, uint32_t *out_bits, ui
                         cudaStream_t s, uint64_t *launches)
 {
     const uint32_t nwords = (n + 31) / 32;
-    cudaError_t e = launch_pdl(k_rank, dim3(1), dim3(1024), 0, s, bits, nwords, out_bits, out_rank, out_list);
+    const dim3 grid((nwords + kRankWords - 1) / kRankWords);
+    cudaError_t e = launch_pdl(k_rank, grid, dim3(1024), 0, s, bits, nwords, out_bits, out_rank, out_list);
     *launches += 1;
     return e;
 }
