@@ -298,7 +298,6 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Shared-memory offset of chunk c (16 bytes) of record q among nrec records
@@ -418,26 +417,25 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, uint32_t lg_cw, uin
 
     if (ntiles > 0) issue(0, buf0);
     cp_async_commit();
-    if (ntiles > 1) issue(1, buf0 + tile_bytes);
-    cp_async_commit();
 
+    // one barrier per tile before it is worked on; past it the previous
+    // tile's buffer takes the next copy
     for (uint32_t t = 0; t < ntiles; t++) {
         uint8_t *data = buf0 + (t & 1u) * tile_bytes;
         const uint32_t sdata = (uint32_t)__cvta_generic_to_shared(data);
-        cp_async_wait1(); // tile t (and the records) have landed for this thread
+        cp_async_wait_all(); // tile t (and the records) have landed for this thread
         if (!SPLIT || t == 0)
             __syncthreads();
         else
             lanes_sync(ln);
+        if (t + 1 < ntiles) issue(t + 1, buf0 + ((t + 1) & 1u) * tile_bytes);
+        cp_async_commit();
         {
             const size_t col = col0 + (size_t)t * col_step;
             const size_t rem = a.S - col;
             const TileOut o{a.dst, a.S, col, a.L0, hibase, lo, rem < cw ? (uint32_t)rem : cw};
             pass_tile<R, INV>(sdata, stab, nlev, lg_w, o, zero_top(a), ln);
         }
-        lanes_sync(ln); // these lanes have read their part of this buffer
-        if (t + 2 < ntiles) issue(t + 2, data);
-        cp_async_commit();
     }
     cp_async_wait_all();
     __syncthreads();
@@ -508,27 +506,33 @@ __device__ __forceinline__ void pass_items(const PassArgs &a, uint32_t lg_cw, ui
     pdl_wait(); // the predecessor's writes are visible from here on
     issue(i0, buf0);
     cp_async_commit();
-    if (i0 + 1 < i1) issue(i0 + 1, buf0 + tile_bytes);
-    cp_async_commit();
 
+    // One barrier per tile before it is worked on (and one inside it between
+    // register rounds): once past it, every thread of these lanes is done with
+    // the previous tile, so the next item's copy goes into that buffer.
     for (uint32_t k = i0; k < i1; k++) {
         uint8_t *data = buf0 + ((k - i0) & 1u) * tile_bytes;
+        uint8_t *next = buf0 + ((k + 1 - i0) & 1u) * tile_bytes;
         const uint32_t sdata = (uint32_t)__cvta_generic_to_shared(data);
         const uint32_t g = k / ntiles + a.g0, t = k - (k / ntiles) * ntiles;
         if (RB == 1 && k != i0 && t == 0) {
             // new group: refill the record buffer once every thread is done
-            // with it, and wait for it together with the tiles in flight
-            if (SPLIT) __syncthreads();
+            // with it, and wait for it together with item k's tile
+            __syncthreads();
             stage_pass_recs<R>(a, nrows, (g >> a.L0) << (a.L0 + nlev), sm);
             cp_async_commit();
-            cp_async_wait_all();
+            if (k + 1 < i1) issue(k + 1, next);
+            cp_async_commit();
+            cp_async_wait1();
             __syncthreads();
         } else {
-            cp_async_wait1(); // item k's tile and records have landed for this thread
+            cp_async_wait_all(); // item k's tile (and records) have landed for this thread
             if (!SPLIT || k == i0 || t == 0)
                 __syncthreads();
             else
                 lanes_sync(ln);
+            if (k + 1 < i1) issue(k + 1, next);
+            cp_async_commit();
         }
         {
             const uint32_t lo = g & ((1u << a.L0) - 1u);
@@ -538,9 +542,6 @@ __device__ __forceinline__ void pass_items(const PassArgs &a, uint32_t lg_cw, ui
             const TileOut o{a.dst, a.S, col, a.L0, hibase, lo, rem < cw ? (uint32_t)rem : cw};
             pass_tile<R, INV>(sdata, stab0 + rec_buf(g), nlev, lg_w, o, zero_top(a), ln);
         }
-        lanes_sync(ln); // these lanes have read their part of this tile (and, unsplit, the group's records)
-        if (k + 2 < i1) issue(k + 2, data);
-        cp_async_commit();
     }
     cp_async_wait_all();
     __syncthreads();
@@ -924,40 +925,39 @@ __device__ __forceinline__ void deriv_items(const DerivArgs &a, uint32_t lg_cw, 
     pdl_wait(); // the predecessor's writes are visible from here on
     issue(i0);
     cp_async_commit();
-    issue(i0 + 1);
-    cp_async_commit();
+    if constexpr (kRing == 3) {
+        issue(i0 + 1);
+        cp_async_commit();
+    }
+    // One barrier per tile before it is worked on (and one inside it between
+    // register rounds): past it every thread is done with item k - 1, so its
+    // slot takes item k + kRing - 1 and the accumulator tile is free.
     for (uint32_t k = i0; k < i1; k++) {
         const uint32_t su = (uint32_t)__cvta_generic_to_shared(slot(k));
         const uint32_t sacc = kX ? su + tile_bytes : sacc0;
         uint32_t hibase, lo, t;
         group(k, hibase, lo, t);
         if (k != i0 && t == 0) {
-            // new group: refill the records (every thread is done with them)
+            // new group: refill the records once every thread is done with them
+            __syncthreads();
             stage_deriv_recs<R, MODE>(a, nrows, hibase, lo, sm);
             cp_async_commit();
-            if constexpr (kRing == 3) {
-                issue(k + 2); // into the slot item k - 1 has left
-                cp_async_commit();
-                cp_async_wait1(); // the records and item k's tile (and k + 1's)
-            } else {
-                cp_async_wait_all();
-            }
-        } else if constexpr (kRing == 3) {
-            issue(k + 2);
+            issue(k + kRing - 1);
             cp_async_commit();
-            cp_async_wait2(); // item k's tile (and, for k = i0, the records)
+            cp_async_wait1(); // the records and item k's tile
         } else {
-            cp_async_wait1();
+            if constexpr (kRing == 3)
+                cp_async_wait1(); // item k's tile (and, for k = i0, the records); k + 1 may be in flight
+            else
+                cp_async_wait_all();
+            __syncthreads();
+            issue(k + kRing - 1);
+            cp_async_commit();
         }
-        __syncthreads();
+        if (k != i0 && t == 0) __syncthreads();
         const size_t col = (size_t)t << lg_cw;
         const size_t rem = a.S - col;
         deriv_tile<R, MODE>(a, su, sacc, s_b, s_binv, lg_w, hibase, lo, col, rem < cw ? (uint32_t)rem : cw);
-        __syncthreads();
-        if constexpr (kRing == 2) {
-            issue(k + 2);
-            cp_async_commit();
-        }
     }
     cp_async_wait_all();
     __syncthreads();
