@@ -841,21 +841,20 @@ __device__ __forceinline__ void deriv_body(const DerivArgs &a, uint32_t lg_cw, u
     };
     if (ntiles > 0) issue(0, stage0);
     cp_async_commit();
-    if (ntiles > 1) issue(1, stage0 + stage_bytes);
-    cp_async_commit();
 
+    // one barrier per tile before it is worked on; past it the previous
+    // tile's stage takes the next copy
     for (uint32_t t = 0; t < ntiles; t++) {
         uint8_t *stage = stage0 + (t & 1u) * stage_bytes;
         const uint32_t su = (uint32_t)__cvta_generic_to_shared(stage), sacc = su + tile_bytes;
         const size_t col = col0 + (size_t)t * col_step;
         const size_t rem = a.S - col;
         const uint32_t width = rem < cw ? (uint32_t)rem : cw;
-        cp_async_wait1();
+        cp_async_wait_all();
         __syncthreads();
-        deriv_tile<R, MODE>(a, su, sacc, s_b, s_binv, lg_w, hibase, lo, col, width);
-        __syncthreads();
-        if (t + 2 < ntiles) issue(t + 2, stage);
+        if (t + 1 < ntiles) issue(t + 1, stage0 + ((t + 1) & 1u) * stage_bytes);
         cp_async_commit();
+        deriv_tile<R, MODE>(a, su, sacc, s_b, s_binv, lg_w, hibase, lo, col, width);
     }
     cp_async_wait_all();
     __syncthreads();
