@@ -24,10 +24,14 @@ namespace lch {
 namespace {
 
 // MODE 0: FWHT(L) -> fl_out.  MODE 1: full locator -> pre/post.
+// MODE 1 with rec_pre / rec_post: also the split-table records of every
+// Pi(j) and 1/Pi'(j) (zero records for the other rows), in the region layout
+// of n records, for the fused short-codeword decode.
 template <int R, int MODE>
 __global__ void __launch_bounds__(1024) k_loc_small(uint32_t lgn, MaskBits bits, const uint16_t *__restrict__ logt,
                                                     const uint16_t *__restrict__ expt, const uint32_t *__restrict__ fl,
-                                                    uint32_t *fl_out, uint16_t *pre, uint16_t *post, uint32_t ninv)
+                                                    uint32_t *fl_out, uint16_t *pre, uint16_t *post, uint32_t ninv,
+                                                    uint8_t *rec_pre, uint8_t *rec_post)
 {
     extern __shared__ uint32_t v[];
     pdl_trigger();
@@ -44,6 +48,17 @@ __global__ void __launch_bounds__(1024) k_loc_small(uint32_t lgn, MaskBits bits,
         fwht_smem<R>(v, lgn);
         for (uint32_t j = threadIdx.x; j < n; j += blockDim.x)
             emit<R>(j, mmul<R>(v[j], ninv), mask_bit(bits, j), expt, pre, post);
+        if (rec_pre) {
+            constexpr uint32_t M = (1u << R) - 1, cpr = FT<R>::rec_bytes / 16;
+            for (uint32_t i = threadIdx.x; i < n * cpr; i += blockDim.x) {
+                const uint32_t q = i / cpr, c = i - q * cpr;
+                const uint32_t cq = mmul<R>(v[q], ninv);
+                const bool e = mask_bit(bits, q);
+                const uint32_t kp = e ? 0u : expt[cq], kd = e ? expt[cq == 0 ? 0 : M - cq] : 0u;
+                *reinterpret_cast<uint4 *>(rec_pre + rec_dst<R>(n, q, c)) = rec_chunk<R>(kp, c);
+                *reinterpret_cast<uint4 *>(rec_post + rec_dst<R>(n, q, c)) = rec_chunk<R>(kd, c);
+            }
+        }
     }
 }
 
@@ -110,7 +125,8 @@ constexpr uint32_t kSmallLg = 12;
 
 template <int R>
 cudaError_t run(int mode, const FieldTables &t, uint32_t lgn, const MaskBits *bits, const uint32_t *fl,
-                uint32_t *fl_out, uint32_t *work, uint16_t *pre, uint16_t *post, cudaStream_t s, uint64_t *launches)
+                uint32_t *fl_out, uint32_t *work, uint16_t *pre, uint16_t *post, cudaStream_t s, uint64_t *launches,
+                uint8_t *rec_pre = nullptr, uint8_t *rec_post = nullptr)
 {
     constexpr uint32_t M = (1u << R) - 1;
     const uint32_t ninv = (uint32_t)((1ull << (R - lgn)) % M);
@@ -122,9 +138,11 @@ cudaError_t run(int mode, const FieldTables &t, uint32_t lgn, const MaskBits *bi
         const unsigned threads = n < 1024 ? (n < 32 ? 32 : n) : 1024;
         const size_t smem = sizeof(uint32_t) * n;
         if (mode == 0)
-            e = launch_pdl(k_loc_small<R, 0>, dim3(1), dim3(threads), smem, s, lgn, mb, t.logt, t.expt, fl, fl_out, pre, post, ninv);
+            e = launch_pdl(k_loc_small<R, 0>, dim3(1), dim3(threads), smem, s, lgn, mb, t.logt, t.expt, fl, fl_out, pre, post, ninv,
+                           (uint8_t *)nullptr, (uint8_t *)nullptr);
         else
-            e = launch_pdl(k_loc_small<R, 1>, dim3(1), dim3(threads), smem, s, lgn, mb, t.logt, t.expt, fl, fl_out, pre, post, ninv);
+            e = launch_pdl(k_loc_small<R, 1>, dim3(1), dim3(threads), smem, s, lgn, mb, t.logt, t.expt, fl, fl_out, pre, post, ninv,
+                           rec_pre, rec_post);
         *launches += 1;
         return e;
     }
@@ -157,10 +175,11 @@ cudaError_t launch_fwht_log_table(int r, const FieldTables &t, uint32_t lgn, uin
 }
 
 cudaError_t launch_locator(int r, const FieldTables &t, uint32_t lgn, const MaskBits &bits, const uint32_t *fl,
-                           uint32_t *work, uint16_t *pre, uint16_t *post, cudaStream_t s, uint64_t *launches)
+                           uint32_t *work, uint16_t *pre, uint16_t *post, cudaStream_t s, uint64_t *launches,
+                           uint8_t *rec_pre, uint8_t *rec_post)
 {
-    if (r == 8) return run<8>(1, t, lgn, &bits, fl, nullptr, work, pre, post, s, launches);
-    return run<16>(1, t, lgn, &bits, fl, nullptr, work, pre, post, s, launches);
+    if (r == 8) return run<8>(1, t, lgn, &bits, fl, nullptr, work, pre, post, s, launches, rec_pre, rec_post);
+    return run<16>(1, t, lgn, &bits, fl, nullptr, work, pre, post, s, launches, rec_pre, rec_post);
 }
 
 } // namespace lch

@@ -126,49 +126,6 @@ template <uint32_t K> struct MulK<8, K> {
     static __device__ __forceinline__ uint32_t f(uint32_t w, const TabRef<8> &t) { return mul8<K * 256>(w, t); }
 };
 
-// Chunk c (16 bytes) of the split-table record of constant k, computed from
-// the products k x^b alone (no tables): entry e of a sub-table whose first
-// power is x^o is the XOR of k x^(o+b) over the set bits b of e.
-__device__ __forceinline__ uint32_t xtime16(uint32_t v)
-{
-    v <<= 1;
-    return (v & 0x10000u) ? v ^ FT<16>::poly : v;
-}
-__device__ __forceinline__ uint32_t xtime8(uint32_t v)
-{
-    v <<= 1;
-    return (v & 0x100u) ? v ^ FT<8>::poly : v;
-}
-template <int R> __device__ __forceinline__ uint4 rec_chunk(uint32_t k, uint32_t c);
-template <> __device__ __forceinline__ uint4 rec_chunk<16>(uint32_t k, uint32_t c)
-{
-    // chunks 0-7: k e (e < 64); 8-15: k (e << 6); 16-17: k (e << 12) (e < 16)
-    const uint32_t o = c < 8 ? 0 : (c < 16 ? 6 : 12), q = c - (c < 8 ? 0 : (c < 16 ? 8 : 16));
-    uint32_t p0 = k;
-    for (uint32_t i = 0; i < o; i++) p0 = xtime16(p0);
-    const uint32_t p1 = xtime16(p0), p2 = xtime16(p1), p3 = xtime16(p2), p4 = xtime16(p3), p5 = xtime16(p4);
-    const uint32_t e0 = ((q & 1u) ? p3 : 0u) ^ ((q & 2u) ? p4 : 0u) ^ ((q & 4u) ? p5 : 0u); // entries 8q .. 8q+7
-    const uint32_t e1 = e0 ^ p0, e2 = e0 ^ p1, e3 = e1 ^ p1;
-    const uint32_t e4 = e0 ^ p2, e5 = e1 ^ p2, e6 = e2 ^ p2, e7 = e3 ^ p2;
-    return make_uint4(e0 | (e1 << 16), e2 | (e3 << 16), e4 | (e5 << 16), e6 | (e7 << 16));
-}
-template <> __device__ __forceinline__ uint4 rec_chunk<8>(uint32_t k, uint32_t c)
-{
-    // entries 16c .. 16c+15 of the 256 products k e
-    uint32_t p[8];
-    p[0] = k;
-#pragma unroll
-    for (int b = 1; b < 8; b++) p[b] = xtime8(p[b - 1]);
-    uint32_t e[16];
-    e[0] = ((c & 1u) ? p[4] : 0u) ^ ((c & 2u) ? p[5] : 0u) ^ ((c & 4u) ? p[6] : 0u) ^ ((c & 8u) ? p[7] : 0u);
-#pragma unroll
-    for (int r = 1; r < 16; r++) e[r] = e[r & (r - 1)] ^ p[(r & 1) ? 0 : (r & 2) ? 1 : (r & 4) ? 2 : 3];
-    uint32_t w[4];
-#pragma unroll
-    for (int i = 0; i < 4; i++) w[i] = e[4 * i] | (e[4 * i + 1] << 8) | (e[4 * i + 2] << 16) | (e[4 * i + 3] << 24);
-    return make_uint4(w[0], w[1], w[2], w[3]);
-}
-
 // Butterflies of local level j (0 <= j < Q) on the 2^Q registers x[], whose
 // row u is tile row base | (u << s0).  The pair (u, u + 2^j) belongs to block
 // (base >> (s0+j+1)) + (u >> (j+1)) of level s0 + j.
@@ -285,12 +242,6 @@ __device__ __forceinline__ void run_round(uint32_t q, uint32_t data, uint32_t ta
     }
 }
 
-template <int R>
-__host__ __device__ __forceinline__ uint32_t tab_bytes(uint32_t nrec)
-{
-    return (nrec * FT<R>::rec_bytes + 127u) & ~127u;
-}
-
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
     const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
@@ -299,16 +250,6 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// Shared-memory offset of chunk c (16 bytes) of record q among nrec records
-// in the region layout of TabRef.
-template <int R> __device__ __forceinline__ uint32_t rec_dst(uint32_t nrec, uint32_t q, uint32_t c)
-{
-    if constexpr (R == 16)
-        return c < 8 ? (q << 7) + (c << 4) : (c < 16 ? ((nrec + q) << 7) + ((c - 8) << 4) : (nrec << 8) + (q << 5) + ((c - 16) << 4));
-    else
-        return (q << 8) + (c << 4);
-}
 
 // Copy the factor records of the row group at hibase (levels [L0, L0+nlev))
 // into the region layout at tab (cp.async; the caller commits).
@@ -807,8 +748,7 @@ template <int R, int MODE>
 __device__ __forceinline__ void deriv_body(const DerivArgs &a, uint32_t lg_cw, uint32_t g, uint32_t y0, uint32_t ystep,
                                            uint8_t *sm)
 {
-    constexpr bool kX = MODE == 1, kMulB = MODE != 1, kInv = MODE != 0;
-    constexpr uint32_t kSets = (kMulB ? 1 : 0) + (kInv ? 1 : 0);
+    constexpr bool kX = MODE == 1, kMulB = MODE != 1;
     const uint32_t nlev = a.nlev, nrows = 1u << nlev;
     const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
     const uint32_t rec_bytes = tab_bytes<R>(nrows);
@@ -1069,6 +1009,7 @@ struct FusedDecArgs {
     const uint8_t *rec;             // factor records of every level
     const uint8_t *brec, *binvrec;  // records of B_j and B_j^-1
     const uint16_t *pre, *post;     // Pi(j) off E (0 on E); 1/Pi'(j) on E (0 off E)
+    const uint8_t *prerec, *postrec; // their records (n, region layout), or null: built here
 };
 
 template <int R>
@@ -1170,11 +1111,16 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_fused_dec(FusedDecArgs a, u
         else
             *reinterpret_cast<uint4 *>(t0 + v * 16) = make_uint4(0, 0, 0, 0);
     }
-    cp_async_commit();
-    for (uint32_t v = threadIdx.x; v < n * cpr; v += blockDim.x) {
-        const uint32_t q = v / cpr, c = v - q * cpr;
-        *reinterpret_cast<uint4 *>(rrec + rec_dst<R>(n, q, c)) = rec_chunk<R>(a.pre[q], c);
+    if (a.prerec) {
+        for (uint32_t v = threadIdx.x; v < tab_bytes<R>(n) / 16; v += blockDim.x)
+            cp_async16(rrec + v * 16, a.prerec + v * 16);
+    } else {
+        for (uint32_t v = threadIdx.x; v < n * cpr; v += blockDim.x) {
+            const uint32_t q = v / cpr, c = v - q * cpr;
+            *reinterpret_cast<uint4 *>(rrec + rec_dst<R>(n, q, c)) = rec_chunk<R>(a.pre[q], c);
+        }
     }
+    cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
     tile_rows_mul<R>(s0, sr, n, lg_w);
@@ -1200,11 +1146,18 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_fused_dec(FusedDecArgs a, u
     __syncthreads();
     tile_rows_mul<R>(s1, sr, n, lg_w); // the derivative's coefficients, B^-1 (sums)
     __syncthreads();
-    for (uint32_t v = threadIdx.x; v < n * cpr; v += blockDim.x) {
-        const uint32_t q = v / cpr, c = v - q * cpr;
-        *reinterpret_cast<uint4 *>(rrec + rec_dst<R>(n, q, c)) = rec_chunk<R>(a.post[q], c);
+    if (a.postrec) {
+        for (uint32_t v = threadIdx.x; v < tab_bytes<R>(n) / 16; v += blockDim.x)
+            cp_async16(rrec + v * 16, a.postrec + v * 16);
+        cp_async_commit();
+    } else {
+        for (uint32_t v = threadIdx.x; v < n * cpr; v += blockDim.x) {
+            const uint32_t q = v / cpr, c = v - q * cpr;
+            *reinterpret_cast<uint4 *>(rrec + rec_dst<R>(n, q, c)) = rec_chunk<R>(a.post[q], c);
+        }
     }
     tile_levels<R, 0>(s1, sf, lgn, lg_w); // hatF' at every point
+    cp_async_wait_all();
     __syncthreads();
     // F(j) = hatF'(j) / Pi'(j), written to the erased rows only
     for (uint32_t it = threadIdx.x; it < (n << lg_w); it += blockDim.x) {
@@ -1779,10 +1732,10 @@ uint32_t fused_dec_lg_cw(int r, uint32_t lgn, size_t S)
 }
 
 cudaError_t launch_fused_decode(int r, const FieldTables &t, uint32_t lgn, uint8_t *shards, size_t S,
-                                const uint16_t *pre, const uint16_t *post, uint32_t lg_cw, cudaStream_t s,
-                                uint64_t *launches)
+                                const uint16_t *pre, const uint16_t *post, const uint8_t *prerec,
+                                const uint8_t *postrec, uint32_t lg_cw, cudaStream_t s, uint64_t *launches)
 {
-    const FusedDecArgs a{shards, S, lgn, t.rec, t.brec, t.binvrec, pre, post};
+    const FusedDecArgs a{shards, S, lgn, t.rec, t.brec, t.binvrec, pre, post, prerec, postrec};
     const dim3 grid((unsigned)((S + (1ull << lg_cw) - 1) >> lg_cw));
     cudaError_t e;
     if (r == 8)

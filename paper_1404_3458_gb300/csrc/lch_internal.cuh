@@ -29,6 +29,68 @@ template <> struct FT<16> {
     static constexpr uint32_t rec_entries = 144;
 };
 
+// ---- split-table records of a constant (the layout the multiply reads)
+// A record set of nrec constants is laid out in regions: GF(2^16) region 0 =
+// nrec x 128 B (c*e, e < 64), region 1 = nrec x 128 B (c*(e<<6)), region 2 =
+// nrec x 32 B (c*(e<<12), e < 16); GF(2^8) nrec x 256 B (c*e).  tab_bytes is
+// the set's size, rec_dst the offset of chunk c (16 bytes) of record q.
+template <int R>
+__host__ __device__ __forceinline__ uint32_t tab_bytes(uint32_t nrec)
+{
+    return (nrec * FT<R>::rec_bytes + 127u) & ~127u;
+}
+template <int R> __device__ __forceinline__ uint32_t rec_dst(uint32_t nrec, uint32_t q, uint32_t c)
+{
+    if constexpr (R == 16)
+        return c < 8 ? (q << 7) + (c << 4) : (c < 16 ? ((nrec + q) << 7) + ((c - 8) << 4) : (nrec << 8) + (q << 5) + ((c - 16) << 4));
+    else
+        return (q << 8) + (c << 4);
+}
+
+// Chunk c (16 bytes) of the split-table record of constant k, computed from
+// the products k x^b alone (no tables): entry e of a sub-table whose first
+// power is x^o is the XOR of k x^(o+b) over the set bits b of e.
+__device__ __forceinline__ uint32_t xtime16(uint32_t v)
+{
+    v <<= 1;
+    return (v & 0x10000u) ? v ^ FT<16>::poly : v;
+}
+__device__ __forceinline__ uint32_t xtime8(uint32_t v)
+{
+    v <<= 1;
+    return (v & 0x100u) ? v ^ FT<8>::poly : v;
+}
+template <int R> __device__ __forceinline__ uint4 rec_chunk(uint32_t k, uint32_t c);
+template <> __device__ __forceinline__ uint4 rec_chunk<16>(uint32_t k, uint32_t c)
+{
+    // chunks 0-7: k e (e < 64); 8-15: k (e << 6); 16-17: k (e << 12) (e < 16)
+    const uint32_t o = c < 8 ? 0 : (c < 16 ? 6 : 12), q = c - (c < 8 ? 0 : (c < 16 ? 8 : 16));
+    uint32_t p0 = k;
+    for (uint32_t i = 0; i < o; i++) p0 = xtime16(p0);
+    const uint32_t p1 = xtime16(p0), p2 = xtime16(p1), p3 = xtime16(p2), p4 = xtime16(p3), p5 = xtime16(p4);
+    const uint32_t e0 = ((q & 1u) ? p3 : 0u) ^ ((q & 2u) ? p4 : 0u) ^ ((q & 4u) ? p5 : 0u); // entries 8q .. 8q+7
+    const uint32_t e1 = e0 ^ p0, e2 = e0 ^ p1, e3 = e1 ^ p1;
+    const uint32_t e4 = e0 ^ p2, e5 = e1 ^ p2, e6 = e2 ^ p2, e7 = e3 ^ p2;
+    return make_uint4(e0 | (e1 << 16), e2 | (e3 << 16), e4 | (e5 << 16), e6 | (e7 << 16));
+}
+template <> __device__ __forceinline__ uint4 rec_chunk<8>(uint32_t k, uint32_t c)
+{
+    // entries 16c .. 16c+15 of the 256 products k e
+    uint32_t p[8];
+    p[0] = k;
+#pragma unroll
+    for (int b = 1; b < 8; b++) p[b] = xtime8(p[b - 1]);
+    uint32_t e[16];
+    e[0] = ((c & 1u) ? p[4] : 0u) ^ ((c & 2u) ? p[5] : 0u) ^ ((c & 4u) ? p[6] : 0u) ^ ((c & 8u) ? p[7] : 0u);
+#pragma unroll
+    for (int r = 1; r < 16; r++) e[r] = e[r & (r - 1)] ^ p[(r & 1) ? 0 : (r & 2) ? 1 : (r & 4) ? 2 : 3];
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) w[i] = e[4 * i] | (e[4 * i + 1] << 8) | (e[4 * i + 2] << 16) | (e[4 * i + 3] << 24);
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+
 // Shift-and-add product with reduction after every doubling ("xtime").
 template <int R>
 __host__ __device__ __forceinline__ uint32_t gf_mul_slow(uint32_t a, uint32_t b)
@@ -214,7 +276,9 @@ cudaError_t launch_deriv(int r, int mode, const DerivArgs &a, cudaStream_t s, ui
 // The decode of Algorithm 2 after the locator, as one launch, for lg n <= 8:
 // fused_dec_lg_cw gives its column-slice width (log2 bytes), 0 when the
 // codeword does not fit the fused form.  pre = Pi off E (0 on E), post =
-// 1/Pi' on E (0 off E); only the erased rows of shards are written.
+// 1/Pi' on E (0 off E); prerec / postrec, when not null, are their records
+// from launch_locator (else each CTA builds them).  Only the erased rows of
+// shards are written.
 uint32_t fused_dec_lg_cw(int r, uint32_t lgn, size_t S);
 // Algorithm 1 as one launch for lg k <= 8 (k a power of two, ncos = n/k - 1
 // cosets written after the message rows); fused_enc_lg_cw as above.
@@ -222,8 +286,8 @@ uint32_t fused_enc_lg_cw(int r, uint32_t lgk, size_t S);
 cudaError_t launch_fused_encode(int r, const FieldTables &t, uint32_t lgk, uint32_t ncos, uint8_t *shards, size_t S,
                                 uint32_t lg_cw, cudaStream_t s, uint64_t *launches);
 cudaError_t launch_fused_decode(int r, const FieldTables &t, uint32_t lgn, uint8_t *shards, size_t S,
-                                const uint16_t *pre, const uint16_t *post, uint32_t lg_cw, cudaStream_t s,
-                                uint64_t *launches);
+                                const uint16_t *pre, const uint16_t *post, const uint8_t *prerec,
+                                const uint8_t *postrec, uint32_t lg_cw, cudaStream_t s, uint64_t *launches);
 
 // c = c (.) t elementwise over `bytes` bytes (Sec. VI.A pointwise product).
 cudaError_t launch_pointwise(int r, uint8_t *c, const uint8_t *t, size_t bytes, const FieldTables &tab,
@@ -305,9 +369,12 @@ cudaError_t launch_rank(const MaskBits &bits, uint32_t n, uint32_t *out_bits, ui
 
 cudaError_t launch_fwht_log_table(int r, const FieldTables &t, uint32_t lgn, uint32_t *fl,
                                   uint32_t *work, cudaStream_t s, uint64_t *launches);
+// rec_pre / rec_post (n <= 4096 only; may be null): also the split-table
+// records of pre and post, in the region layout of n records.
 cudaError_t launch_locator(int r, const FieldTables &t, uint32_t lgn, const MaskBits &bits,
                            const uint32_t *fl, uint32_t *work, uint16_t *pre, uint16_t *post,
-                           cudaStream_t s, uint64_t *launches);
+                           cudaStream_t s, uint64_t *launches, uint8_t *rec_pre = nullptr,
+                           uint8_t *rec_post = nullptr);
 
 // ---------------------------------------------------------------- batches
 // One persistent launch runs many codewords: tasks are pulled from a queue in
