@@ -1726,7 +1726,8 @@ uint32_t fused_dec_lg_cw(int r, uint32_t lgn, size_t S)
         fit++;
     if (fit < 4) return 0;
     // slices of about S / 128 bytes (at least 16): enough CTAs to spread a
-    // short codeword over the SMs
+    // short codeword over the SMs; narrower ones cost more than the waves
+    // they save (medium_gf16 decode: 102 us at 128-byte slices, 127 at 64)
     const uint32_t want = std::max<uint32_t>(4u, ilog2(std::max<size_t>(S >> 7, 1)));
     return std::min(fit, want);
 }
