@@ -1747,6 +1747,8 @@ cudaError_t launch_fused_decode(int r, const FieldTables &t, uint32_t lgn, uint8
     return e;
 }
 
+// As fused_dec_lg_cw; for the encode wider slices measured faster still
+// (medium_gf16: 23.7 us at 512-byte slices, 27.7 at 256, 34.2 at 128).
 uint32_t fused_enc_lg_cw(int r, uint32_t lgk, size_t S)
 {
     if (lgk < 1 || lgk > 8) return 0;
