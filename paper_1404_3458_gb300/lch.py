@@ -127,7 +127,7 @@ def _stream_handle(stream):
 def _buf(t, rows=None):
     import torch
 
-    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.uint8:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.uint8:
         raise TypeError("expected a CUDA uint8 tensor of shape [rows, shard_bytes]")
     if t.dim() != 2 or not t.is_contiguous():
         raise ValueError("expected a contiguous 2-D tensor [rows, shard_bytes]")
@@ -350,8 +350,7 @@ class Context:
         m = np.ascontiguousarray(np.asarray(erasure_mask, dtype=np.uint8).reshape(-1))
         if m.size != n:
             raise ValueError(f"erasure mask must have n={n} entries")
-        _check(load().rs_decode(self._h, n, k, field, p, S, m.ctypes.data_as(ctypes.c_void_p),
-                                _stream_handle(stream)))
+        _check(load().rs_decode(self._h, n, k, field, p, S, m.ctypes.data, _stream_handle(stream)))
 
     # Algorithm 2 from the received shards alone: `received` holds the
     # n - |E| surviving shards in row order, `recovered` gets the |E| erased
@@ -365,5 +364,4 @@ class Context:
         po, S2 = _buf(recovered, ne)
         if S2 != S:
             raise ValueError("received and recovered shards differ in size")
-        _check(load().rs_decode_packed(self._h, n, k, field, pr, po, S, m.ctypes.data_as(ctypes.c_void_p),
-                                       _stream_handle(stream)))
+        _check(load().rs_decode_packed(self._h, n, k, field, pr, po, S, m.ctypes.data, _stream_handle(stream)))
