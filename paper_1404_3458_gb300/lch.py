@@ -148,12 +148,12 @@ def _rows_args(src, dst, idx):
     import torch
 
     for t in (src, dst):
-        if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.uint8 or t.dim() != 2 \
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.uint8 or t.dim() != 2 \
                 or not t.is_contiguous():
             raise TypeError("expected contiguous CUDA uint8 tensors [rows, shard_bytes]")
     if src.shape[1] != dst.shape[1]:
         raise ValueError("src and dst must have the same shard_bytes")
-    if not isinstance(idx, torch.Tensor) or idx.device.type != "cuda" or idx.dtype != torch.int32 or idx.dim() != 1 \
+    if not isinstance(idx, torch.Tensor) or not idx.is_cuda or idx.dtype != torch.int32 or idx.dim() != 1 \
             or not idx.is_contiguous():
         raise TypeError("expected a contiguous CUDA int32 index tensor")
     return ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()), ctypes.c_void_p(idx.data_ptr()), \

@@ -104,3 +104,20 @@ def test_utility_entry_points_check_arguments(L):
     assert L.lch_rows_scatter(vp(16), vp(16), vp(16), 4, 40, None) == lch.LCH_EINVAL
     assert L.lch_rows_scatter(vp(8), vp(16), vp(16), 4, 64, None) == lch.LCH_EINVAL      # misaligned
     assert L.lch_rows_gather(None, None, None, 0, 64, None) == lch.LCH_OK                 # count 0: no-op
+
+
+def test_binding_refuses_host_tensors_before_any_call():
+    """The Python binding marshals only CUDA uint8 tensors: host tensors and
+    wrong shapes are refused before the library is called."""
+    import numpy as np
+    import torch
+
+    with pytest.raises(TypeError):
+        lch._buf(torch.zeros((4, 16), dtype=torch.uint8))            # host memory
+    with pytest.raises(TypeError):
+        lch._buf(np.zeros((4, 16), dtype=np.uint8))                   # not a tensor
+    with pytest.raises(TypeError):
+        lch.rows_gather(torch.zeros((4, 16), dtype=torch.uint8), torch.zeros((4, 16), dtype=torch.uint8),
+                        torch.zeros(4, dtype=torch.int32))
+    with pytest.raises(TypeError):
+        lch.derivative_noalloc(16, torch.zeros((8, 16), dtype=torch.uint8))
