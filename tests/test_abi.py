@@ -121,3 +121,47 @@ def test_binding_refuses_host_tensors_before_any_call():
                         torch.zeros(4, dtype=torch.int32))
     with pytest.raises(TypeError):
         lch.derivative_noalloc(16, torch.zeros((8, 16), dtype=torch.uint8))
+
+
+C_CLIENT = r"""
+#include "lch.h"
+#include <stdio.h>
+#include <string.h>
+
+int main(void) {
+    unsigned char mask[32] = {0};
+    mask[3] = 1;
+    void *fake = (void *)0x10000;                       /* never dereferenced */
+    if (rs_decode(0, 32, 16, LCH_GF8, fake, 1024, mask, 0) != LCH_EINVAL) return 1;
+    if (!strstr(lch_last_error(), "ctx is NULL")) return 2;
+    if (rs_encode(0, 33, 16, LCH_GF8, fake, 1024, 0) != LCH_EINVAL) return 3;
+    if (rs_decode_packed(0, 32, 16, LCH_GF8, fake, fake, 1000, mask, 0) != LCH_EINVAL) return 4;
+    if (strcmp(lch_strerror(LCH_ETOOMANY), "more erasures than n - k") != 0) return 5;
+    lch_ctx *ctx = 0;
+    int rc = lch_ctx_create(&ctx, 0);                   /* LCH_OK with a GPU, LCH_ECUDA without */
+    if (rc == LCH_OK) lch_ctx_destroy(ctx);
+    else if (rc != LCH_ECUDA) return 6;
+    printf("ok\n");
+    return 0;
+}
+"""
+
+
+def test_header_is_a_plain_c_abi(L, tmp_path):
+    """include/lch.h compiles as C99 with warnings as errors, and a C program
+    links liblch.so and gets the documented argument checks (no compute)."""
+    import os
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(lch.LIB_PATH)
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.dirname(lch.HEADER),
+                    str(src), "-L", libdir, "-llch", f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
