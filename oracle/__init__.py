@@ -2,5 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and
 the CPU-baseline leg of ``bench.py``.  The product library never imports it.
+``oracle.fastcpu`` (not imported here) is a CPU restatement of the paper's fast
+algorithms, pinned to the oracle by the tests and used only for comparison
+timings on a CPU core.
 """
 from .oracle import *  # noqa: F401,F403
