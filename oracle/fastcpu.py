@@ -2,10 +2,11 @@
 CPU core.
 
 TEST AND BASELINE INFRASTRUCTURE ONLY, like the oracle beside it, and not the
-oracle: it runs the same butterflies, derivative and locator as the paper's
-own CPU program, so that the method's speed on a CPU core can be set beside
-the paper's figures (Sec. VI.B: about 1.12 s to encode and 3.06 s to decode
-n = 2^16, k = 2^15 on an Intel Core i7-950).  The tests pin it to the oracle.
+oracle: it runs the paper's butterflies, derivative and locator on a CPU
+core, as the paper's own timings did, so that the method's CPU speed can be
+set beside the paper's figures (Sec. VI.B: about 1.12 s to encode and 3.06 s
+to decode n = 2^16, k = 2^15 on an Intel Core i7-950) and beside the GPU
+library.  The tests pin it to the oracle.
 
 ``python -m oracle.fastcpu`` times one encode and one decode of n = 65536,
 k = 32768 with 32768 random erasures over GF(2^16), one element per symbol
