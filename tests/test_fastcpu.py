@@ -60,3 +60,17 @@ def test_decode_every_pattern_of_8_4():
     erased = np.ones(n, dtype=np.uint8)
     with pytest.raises(ValueError):
         FC.rs_decode(r, n, k, enc, erased)  # more than n - k erasures
+
+
+def test_full_size_encode_matches_the_oracle_on_sampled_rows():
+    """n = 65536, k = 32768 over GF(2^16): four parity rows of one column, the
+    first, second, a middle and the last, against the oracle's Lagrange
+    evaluation."""
+    from paper_1404_3458_gb300 import workloads as WL
+
+    n, k = 65536, 32768
+    msg = np.zeros((n, 1), dtype=np.uint16)
+    msg[:k, 0] = O.to_elems(WL.shards(k, 2, seed=WL.SEED_BASE + 9), 16)[:, 0]
+    enc = FC.rs_encode(16, n, k, msg)
+    rows = k + np.array([0, 1, 12345, n - k - 1])
+    assert np.array_equal(enc[rows], O.rs_encode(16, n, k, msg, rows=rows)[rows])

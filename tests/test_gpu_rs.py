@@ -154,6 +154,19 @@ def test_large_gf16_workload(ctx):
         assert np.array_equal(gpu_decode(ctx, w.field, w.n, w.k, cw, mask), cw)
 
 
+def test_large_gf16_encode_matches_the_cpu_restatement(ctx):
+    """n = 65536, k = 32768, 4 KiB shards: all 32768 parity rows of 64 element
+    columns against the CPU restatement of the paper's fast algorithms
+    (oracle/fastcpu.c, itself pinned to the oracle, at this size too)."""
+    from oracle import fastcpu as FC
+
+    w = WL.WORKLOADS["large_gf16"]
+    host = message(w.n, w.k, w.shard_bytes, w.seed + 1)
+    cw = gpu_encode(ctx, w.field, w.n, w.k, host)
+    cols = elem_cols(w.shard_bytes, w.field, 64, seed=11)
+    assert np.array_equal(elems(cw, w.field, cols), FC.rs_encode(w.field, w.n, w.k, elems(host, w.field, cols)))
+
+
 def test_shortened_encode_reuses_cached_locator():
     """k not a power of two: the locator of E = {k..n-1} is computed once per
     (field, n, k) and reused by later calls and by batches; every use gives the
