@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(PassArgs a, uint32_t l
 
 // Persistent form: one CTA per SM takes a contiguous range of the
 // (row group, column tile) items in group-major order, with two tile buffers
-// (the tile after next is copied in while the current one is transformed).
+// (the next tile is copied in while the current one is transformed).
 // RB = 2: two record buffers, the next group's records are copied in ahead
 // (needs at least two tiles per group, so that at most two groups are live);
 // RB = 1: one record buffer, refilled when the CTA reaches a new group (a
