@@ -183,11 +183,11 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- our arm
 
-def alu_peak_gmuls(sm_mhz):
+def alu_peak_gmuls(sm_mhz, sms):
     """Integer-pipe ceiling of the split-table GF(2^16) multiply-add: each pair
     of packed elements needs 12 index ops (shift, mask|base), 4 combines and 1
     XOR on the 64-lane ALU pipe, i.e. 8.5 ALU ops per element."""
-    return 152 * 64 * sm_mhz * 1e6 / 8.5 / 1e9
+    return sms * 64 * sm_mhz * 1e6 / 8.5 / 1e9
 
 
 def pct(xs, q):
@@ -286,14 +286,15 @@ def run_ours(args):
     dom = max(kinds, key=lambda kk: kinds[kk]["ms"])
     d = kinds[dom]
     sm_mhz = clk.summary_cache.get("sm_mhz") or 2070.0
-    alu_peak = alu_peak_gmuls(sm_mhz)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = alu_peak_gmuls(sm_mhz, sms)
     achieved_mul = d["mults"] / (d["ms"] / 1e3) / 1e9 if d["ms"] else 0.0
     achieved_gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] else 0.0
     roofline = {"bound": "alu", "kernel": "k_pass (transform butterfly pass)", "achieved": round(achieved_mul, 2),
                 "peak": round(alu_peak, 2), "unit": "Gmul/s", "frac": round(achieved_mul / alu_peak, 4),
-                "peak_source": (f"derived: 152 SMs x 64 ALU lanes/clk x {sm_mhz:.0f} MHz / 8.5 ALU ops per "
+                "peak_source": (f"derived: {sms} SMs x 64 ALU lanes/clk x {sm_mhz:.0f} MHz / 8.5 ALU ops per "
                                 "GF(2^16) split-table multiply-add"),
-                "alu_pipe": {"peak_tops": round(152 * 64 * sm_mhz * 1e6 / 1e12, 2), "ops_per_mult": 8.5,
+                "alu_pipe": {"peak_tops": round(sms * 64 * sm_mhz * 1e6 / 1e12, 2), "ops_per_mult": 8.5,
                              "achieved_tops": round(achieved_mul * 8.5 / 1e3, 2)},
                 "traffic": KPASS_TRAFFIC["bytes"], "traffic_alg_bytes": KPASS_TRAFFIC["alg_bytes"],
                 "traffic_launch": KPASS_TRAFFIC["launch"], "launches_per_step": d["launches"] / args.steps,
@@ -302,6 +303,7 @@ def run_ours(args):
                         "frac": round(achieved_gbs / hbm, 4), "peak_source": f"{hbm_src} hbm_gbs"}}
     alg_bytes = 2 * n * S  # encode n*S + decode n*S per step
     step_ms = ms / args.steps
+    burst = run_burst(ctx, torch, buf, host, w, args, rank)
 
     e2e = None
     if not args.no_e2e:
@@ -332,6 +334,8 @@ def run_ours(args):
     }
     if e2e:
         out["e2e"] = e2e
+    out["burst_decode"] = burst
+    out["cold_first_call"] = run_cold(torch, host, mask, w, local)
     if not args.no_small:
         out["small_configs"] = run_small_latency(ctx, torch, rank)
     if not args.no_batch:
@@ -339,10 +343,79 @@ def run_ours(args):
     if not args.no_serve:
         out["serving"] = run_serving(ctx, torch, args, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w, n, k, S, ne)
+        out["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()
+
+
+def run_burst(ctx, torch, buf, host, w, args, rank):
+    """The workload's second erasure pattern: one contiguous burst of |E| rows
+    at a seeded start.  Per-call decode latency (200 calls, CUDA events) and
+    the step (encode + burst decode) timed like the headline, on the same
+    resident codeword."""
+    r, n, k, S = w.field, w.n, w.k, w.shard_bytes
+    start = WL.random_burst_start(n, w.erasures, w.seed + 200 + rank)
+    mask = WL.burst_mask(n, w.erasures, start)
+    ne = int(mask.sum())
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        ctx.rs_encode(n, k, r, buf)
+        ctx.rs_decode(n, k, r, buf, mask)
+    torch.cuda.synchronize()
+    reps = 200
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+    for i in range(reps):
+        ev[2 * i].record(stream)
+        ctx.rs_decode(n, k, r, buf, mask)
+        ev[2 * i + 1].record(stream)
+    torch.cuda.synchronize()
+    dec = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(reps)]
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        ctx.rs_encode(n, k, r, buf)
+        ctx.rs_decode(n, k, r, buf, mask)
+    z.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(z) / args.steps
+    check = torch.from_numpy(host).cuda()
+    ctx.rs_encode(n, k, r, check)
+    torch.cuda.synchronize()
+    return {"erasures": ne, "burst_rows": [start, start + ne], "decode_ms_p50": round(pct(dec, 50), 4),
+            "decode_ms_p99": round(pct(dec, 99), 4), "ms_per_step": round(ms, 4),
+            "value": round((k + ne) * S / (ms / 1e3) / 1e9, 3), "unit": UNIT,
+            "verified": bool(torch.equal(check, buf))}
+
+
+def run_cold(torch, host, mask, w, device):
+    """First calls on a fresh context (host wall clock, synchronised): the
+    first encode builds the field tables (7 launches) and allocates scratch;
+    the first decode also builds FWHT(log) for lg n and allocates its scratch.
+    Plans are the untuned defaults.  The second pair is warm."""
+    from paper_1404_3458_gb300 import lch
+
+    r, n, k, S = w.field, w.n, w.k, w.shard_bytes
+    buf = torch.from_numpy(host).cuda()
+    torch.cuda.synchronize()
+    t = [time.perf_counter()]
+    c2 = lch.Context(device)
+    torch.cuda.synchronize()
+    t.append(time.perf_counter())
+    for _ in range(2):
+        c2.rs_encode(n, k, r, buf)
+        torch.cuda.synchronize()
+        t.append(time.perf_counter())
+        c2.rs_decode(n, k, r, buf, mask)
+        torch.cuda.synchronize()
+        t.append(time.perf_counter())
+    c2.close()
+    d = [1e3 * (b - a) for a, b in zip(t, t[1:])]
+    return {"context_create_ms": round(d[0], 3), "first_encode_ms": round(d[1], 3),
+            "first_decode_ms": round(d[2], 3), "warm_encode_ms": round(d[3], 3), "warm_decode_ms": round(d[4], 3),
+            "clock": "host wall clock around each call, synchronised",
+            "what": ("fresh context: first encode builds the GF(2^16) tables (7 launches) and allocates scratch; "
+                     "first decode builds FWHT(log) for lg n = 16; default (untuned) pass plans")}
 
 
 def run_batch_compare(ctx, torch, args, rank):
@@ -566,7 +639,7 @@ def run_e2e(ctx, torch, host, mask, w, args):
     h2d, comp, d2h = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     freed_e, freed_d = [None] * NB, [None] * NB  # slot's last copy out has finished
 
-    def step(i):
+    def step(i, compute=True):
         b = i % NB
         ev = [torch.cuda.Event() for _ in range(4)]
         with torch.cuda.stream(h2d):
@@ -579,10 +652,12 @@ def run_e2e(ctx, torch, host, mask, w, args):
             pin_dev[b].copy_(surv_host, non_blocking=True)     # surviving shards in
             ev[1].record(h2d)
         comp.wait_event(ev[0])
-        ctx.rs_encode(n, k, r, enc[b], stream=comp)
+        if compute:
+            ctx.rs_encode(n, k, r, enc[b], stream=comp)
         ev[2].record(comp)
         comp.wait_event(ev[1])
-        ctx.rs_decode_packed(n, k, r, pin_dev[b], pout_dev[b], mask, stream=comp)
+        if compute:
+            ctx.rs_decode_packed(n, k, r, pin_dev[b], pout_dev[b], mask, stream=comp)
         ev[3].record(comp)
         with torch.cuda.stream(d2h):
             d2h.wait_event(ev[2])
@@ -610,82 +685,193 @@ def run_e2e(ctx, torch, host, mask, w, args):
     last = (steps - 1) % NB
     ok = bool(torch.equal(rec_out[last], truth[torch.from_numpy(erased).long()])) and \
         bool(torch.equal(parity_out[last], truth[k:]))
+    # the same schedule with the kernels left out: what the host link alone
+    # takes for the step's copies (their bytes and stream order unchanged)
+    a2, z2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a2.record(h2d)
+    for i in range(steps):
+        step(i, compute=False)
+    z2.record(d2h)
+    torch.cuda.synchronize()
+    copy_ms = a2.elapsed_time(z2) / steps
     return {"value": round((k + ne) * S / (ms / 1e3) / 1e9, 3), "unit": UNIT,
             "h2d_bytes_per_step": (k + ns) * S, "d2h_bytes_per_step": (n - k + ne) * S,
-            "ms_per_step": round(ms, 4), "pipelined": f"{NB} buffer sets, 3 streams",
+            "ms_per_step": round(ms, 4), "copy_only_ms_per_step": round(copy_ms, 4),
+            "copy_gbs_each_way": round(((k + ns) * S + (n - k + ne) * S) / 2 / (copy_ms / 1e3) / 1e9, 2),
+            "pipelined": f"{NB} buffer sets, 3 streams",
             "received": "surviving shards only (packed); recovered shards packed (rs_decode_packed)",
             "verified": ok}
 
 
 # --------------------------------------------------------------------------- CPU oracle
 
-def oracle_sample(w, n, k, S, ne, rows_per_call=8, cols=4, seed=0, encode=True, decode=True):
-    """Time the oracle on a bounded sample of one encode and/or one decode of
-    the workload: each call computes its barycentric weights over all k points
-    (a fixed per-call cost) and then `rows_per_call` rows of `cols` element
-    columns.  Returns (encode s, decode s, equivalent shard bytes of each)."""
-    from oracle import oracle as O
+def host_cpu():
+    """CPU model and core count of this host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    import platform
 
-    r = w.field
-    E = S // (r // 8)
-    g = np.random.default_rng(seed)
-    colsel = np.sort(g.choice(E, cols, replace=False))
+    return {"model": model or "unknown", "nproc": os.cpu_count(), "machine": platform.machine()}
+
+
+def _oracle_job(job):
+    """One single-threaded timing job in a worker process.
+
+    ("enc" | "dec", rows, seed, workload): one oracle rs_encode / rs_decode
+    call of the workload over all element columns, evaluating `rows` parity
+    (or erased) rows; rows = 0 evaluates none, so the call is only the
+    barycentric weights over the k interpolation points (O(k^2), paid once
+    per call).  ("fast", 0, seed, workload): one encode and one decode of the
+    whole workload by the O(n lg n) CPU restatement.  Returns seconds."""
+    kind, nrows, seed, wname = job
+    w = WL.WORKLOADS[wname]
+    r, n, k, S = w.field, w.n, w.k, w.shard_bytes
     host = np.zeros((n, S), dtype=np.uint8)
     host[:k] = WL.shards(k, S, w.seed)
-    el = O.to_elems(host, r)[:, colsel].copy()
     mask = WL.erasure_mask(n, w.erasures, w.seed + 100)
-    erow = np.nonzero(mask)[0]
-    prow = np.sort(g.choice(np.arange(k, n), rows_per_call, replace=False))
-    drow = np.sort(g.choice(erow, rows_per_call, replace=False))
+    g = np.random.default_rng(seed)
+    from oracle import oracle as O
+
+    el = O.to_elems(host, r)
+    if kind == "fast":
+        from oracle import fastcpu as FC
+
+        FC.transform(r, 0, np.zeros((2, 1), dtype=np.uint16))  # its field tables, before timing
+        t0 = time.perf_counter()
+        enc = FC.rs_encode(r, n, k, el)
+        t1 = time.perf_counter()
+        FC.rs_decode(r, n, k, enc, mask)
+        t2 = time.perf_counter()
+        return (t1 - t0, t2 - t1)
+    O.gf_mul(r, 1, 1)  # library loaded before timing
+    pool = np.arange(k, n) if kind == "enc" else np.nonzero(mask)[0]
+    rows = np.sort(g.choice(pool, nrows, replace=False)).astype(np.int32) if nrows else np.zeros(0, np.int32)
     t0 = time.perf_counter()
-    if encode:
-        O.rs_encode(r, n, k, el, rows=prow)
-    t1 = time.perf_counter()
-    if decode:
-        O.rs_decode(r, n, k, el, mask, rows=drow)
-    t2 = time.perf_counter()
-    # fraction of a full step that the sample represents, per call
-    f_enc = (rows_per_call * cols) / ((n - k) * E) if encode else 0.0
-    f_dec = (rows_per_call * cols) / (ne * E) if decode else 0.0
-    return t1 - t0, t2 - t1, f_enc * k * S, f_dec * ne * S
+    if kind == "enc":
+        O.rs_encode(r, n, k, el, rows=rows)
+    else:
+        O.rs_decode(r, n, k, el, mask, rows=rows)
+    return time.perf_counter() - t0
 
 
-def cpu_baseline(w, n, k, S, ne):
-    te, td, be, bd = oracle_sample(w, n, k, S, ne)
-    return {"value": round((be + bd) / (te + td) / 1e9, 12), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"one oracle encode (8 parity rows) and one decode (8 erased rows) of {w.name}, "
-                       f"4 element columns each; value = the sample's share of a step's shard data / its time "
-                       f"({te + td:.2f} s; each call also pays the O(k^2) barycentric weights)")}
+def _run_jobs(jobs, workers):
+    """Run timing jobs in `workers` spawned processes (spawn: no fork of a
+    CUDA-initialised parent)."""
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(processes=workers) as pool:
+        return pool.map(_oracle_job, jobs, chunksize=1)
+
+
+def oracle_extrapolate(w, rows, t_wenc, t_wdec, t_enc, t_dec):
+    """A whole step of the oracle, extrapolated from timed calls: per call, the
+    weights (t_w*) once, then the measured per-row cost ((t - t_w) / rows,
+    every element column) times the rows a step evaluates ((n - k) parity
+    rows, |E| erased rows)."""
+    ne = w.erasures
+    per_enc = max(t_enc - t_wenc, 0.0) / rows
+    per_dec = max(t_dec - t_wdec, 0.0) / rows
+    step_s = t_wenc + (w.n - w.k) * per_enc + t_wdec + ne * per_dec
+    return step_s, per_enc, per_dec
+
+
+def cpu_baseline(w, rows=64):
+    """The oracle's whole-step time, extrapolated (see oracle_extrapolate), and
+    the O(n lg n) CPU restatement's measured whole step, each one core.  The
+    four single-threaded oracle calls run side by side in four processes; the
+    O(n lg n) step runs alone after them (it is memory-bound, and running
+    beside the others slowed it by about half)."""
+    rows = min(rows, w.n - w.k, w.erasures)
+    jobs = [("enc", 0, 1, w.name), ("enc", rows, 1, w.name), ("dec", 0, 2, w.name), ("dec", rows, 2, w.name)]
+    t0 = time.perf_counter()
+    twe, te, twd, td = _run_jobs(jobs, len(jobs))
+    wall = time.perf_counter() - t0
+    fe, fd = _run_jobs([("fast", 0, 3, w.name)], 1)[0]
+    step_s, pe, pd = oracle_extrapolate(w, rows, twe, twd, te, td)
+    data = (w.k + w.erasures) * w.shard_bytes
+    cpu = host_cpu()
+    return {"value": round(data / step_s / 1e9, 9), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "extrapolated": True, "host_cpu": cpu,
+            "sample": (f"oracle rs_encode and rs_decode of {w.name} over all {w.shard_bytes // (w.field // 8)} "
+                       f"element columns: one call each evaluating {rows} rows and one each evaluating none "
+                       f"(barycentric weights only: {twe:.2f} s / {twd:.2f} s); per row {pe * 1e3:.1f} ms "
+                       f"(encode) / {pd * 1e3:.1f} ms (decode); step extrapolated to {w.n - w.k} parity + "
+                       f"{w.erasures} erased rows = {step_s:.0f} s on one core; the 4 single-threaded calls "
+                       f"ran side by side ({wall:.1f} s wall)"),
+            "oracle_step_s_extrapolated": round(step_s, 1),
+            "fast_onlgn": {"value": round(data / (fe + fd) / 1e9, 6), "unit": UNIT, "cores": 1,
+                           "encode_s": round(fe, 3), "decode_s": round(fd, 3), "extrapolated": False,
+                           "what": ("oracle/fastcpu.c: the paper's O(n lg n) transform, derivative and locator in "
+                                    "plain single-threaded C (pinned to the oracle), one whole encode + decode "
+                                    "step of the workload, measured")}}
 
 
 def run_reference(args):
+    """The reference arm: the oracle (the repository's plain-definition
+    checker) on the host cores.  A step is one oracle call over all element
+    columns evaluating a fixed sample of 32 rows (fewer if the code has fewer): an encode (even steps) or a
+    decode (odd steps).  Steps run side by side in a pool of worker processes,
+    one single-threaded call each.  Two further calls evaluate no rows (the
+    barycentric weights alone), so the per-row cost is the call time less the
+    weights; value = the step's shard data over the whole-step time
+    extrapolated from those (weights once per call, per-row cost times the
+    rows of a step)."""
     world, rank, _ = dist_setup(False)
     if rank != 0:
         return
     w = WL.WORKLOADS[args.workload]
     n, k, S = w.n, w.k, w.shard_bytes
     ne = w.erasures
-    times, byts = [], []
-    # each step samples the encode or (odd steps) the decode, so that one step
-    # stays near 7 s (each oracle call pays O(k^2) for its barycentric weights)
-    for i in range(args.warmup + args.steps):
-        te, td, be, bd = oracle_sample(w, n, k, S, ne, rows_per_call=2, cols=2, seed=i,
-                                       encode=(i % 2 == 0), decode=(i % 2 == 1))
-        if i >= args.warmup:
-            times.append(te + td)
-            byts.append(be + bd)
-    value = sum(byts) / sum(times) / 1e9
-    out = {"metric": METRIC, "value": round(value, 12), "unit": UNIT, "impl": "reference", "n_gpus": 1,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 2),
+    rows = min(32, n - k, ne)
+    total = args.warmup + args.steps
+    workers = max(2, min(total + 2, (os.cpu_count() or 2) - 1, 16))
+    jobs = [("enc", 0, 0, w.name), ("dec", 0, 0, w.name)]
+    jobs += [("enc" if i % 2 == 0 else "dec", rows, 1000 + i, w.name) for i in range(total)]
+    t0 = time.perf_counter()
+    res = _run_jobs(jobs, workers)
+    wall = time.perf_counter() - t0
+    twe, twd = res[0], res[1]
+    timed = res[2 + args.warmup:]
+    kinds = ["enc" if i % 2 == 0 else "dec" for i in range(total)][args.warmup:]
+    te = [t for t, kd in zip(timed, kinds) if kd == "enc"] or [twe]
+    td = [t for t, kd in zip(timed, kinds) if kd == "dec"] or [twd]
+    step_s, pe, pd = oracle_extrapolate(w, rows, twe, twd, statistics.mean(te), statistics.mean(td))
+    value = (k + ne) * S / step_s / 1e9
+    cpu = host_cpu()
+    sample = (f"per step: one oracle call over all {S // (w.field // 8)} element columns of {w.name} evaluating "
+              f"{rows} rows, an encode (even steps) or a decode (odd steps); two more calls evaluate no rows "
+              f"(weights only: {twe:.2f} / {twd:.2f} s); per row {pe * 1e3:.1f} / {pd * 1e3:.1f} ms; value = "
+              f"(k + |E|) S over the whole step extrapolated to {n - k} parity + {ne} erased rows "
+              f"({step_s:.0f} s on one core); {workers} single-threaded calls ran side by side "
+              f"({wall:.0f} s wall)")
+    out = {"metric": METRIC, "value": round(value, 9), "unit": UNIT, "impl": "reference", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * statistics.mean(timed), 1) if timed else None,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
            "data": "synthetic",
            "config": {"workload": w.name, "field": f"GF(2^{w.field})", "n": n, "k": k, "shard_bytes": S,
-                      "erasures": ne, "step": "oracle rs_encode or rs_decode (alternating) on a bounded sample"},
-           "cpu_baseline": {"value": round(value, 12), "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": ("per step: one oracle encode (even steps) or one decode (odd steps) of "
-                                       "2 rows x 2 element columns of large_gf16; value = the samples' share of "
-                                       "the shard data / their time")},
-           "e2e": {"value": round(value, 12), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                      "erasures": ne, "step": f"one oracle rs_encode or rs_decode call on a fixed {rows}-row sample"},
+           "cpu_baseline": {"value": round(value, 9), "unit": UNIT, "cores": workers, "kind": "oracle",
+                            "extrapolated": True, "host_cpu": cpu, "sample": sample},
+           "e2e": {"value": round(value, 9), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 

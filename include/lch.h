@@ -98,7 +98,8 @@ LCH_API int lch_derivative(lch_ctx *ctx, int field, uint32_t h, void *buf, size_
  * that its host forbids to allocate, or a latency-critical loop that cannot
  * afford the implicit synchronisation of cudaMalloc/cudaFree).  It computes the
  * same result as lch_derivative but takes no context: its scratch (at most
- * 16 MiB, so h * shard_bytes <= 16777216, else LCH_EINVAL) and its B tables
+ * 16 MiB, so h * shard_bytes <= 16777216 for h >= 2, else LCH_EINVAL; h = 1
+ * only zeroes the row and has no size limit) and its B tables
  * are file-scope device arrays that every GPU loading the library keeps until
  * the process exits.  It runs on the current CUDA device.  The first call on a
  * device sets those arrays up and synchronises `stream` once; make that first

@@ -22,6 +22,7 @@
 // k_pointwise (product of two vectors), and small helpers (broadcast, row
 // gather/scatter, fill).
 #include <algorithm>
+#include <atomic>
 
 #include "lch_internal.cuh"
 
@@ -32,8 +33,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kPassThreads = 512;
 constexpr uint32_t kTileBytes = 32768; // data bytes per tile
-constexpr int kTargetCtas = 152 * 8;
-constexpr int kSms = 152;
 constexpr size_t kPassSmem = 220 * 1024; // dynamic shared memory of the pass kernels
 #ifndef LCH_SPLIT_LG_CW
 #define LCH_SPLIT_LG_CW 8
@@ -1262,7 +1261,7 @@ uint32_t pick_lg_cw(uint32_t nrows, size_t S)
 dim3 pick_grid(uint32_t ngroups, size_t S, uint32_t lg_cw)
 {
     size_t ntiles = (S + (1ull << lg_cw) - 1) >> lg_cw;
-    size_t want = (kTargetCtas + ngroups - 1) / ngroups;
+    size_t want = ((size_t)device_sms() * 8 + ngroups - 1) / ngroups;
     size_t y = want < ntiles ? want : ntiles;
     if (y < 1) y = 1;
     if (y > 65535) y = 65535;
@@ -1294,7 +1293,7 @@ cudaError_t pass_impl(const PassArgs &a, cudaStream_t s)
     const uint64_t items = (uint64_t)ngroups * ntiles;
     if (ntiles >= 2 && items < (1ull << 32)) {
         // persistent form: two record sets when they fit beside the tiles
-        const uint32_t ctas = (uint32_t)std::min<uint64_t>(items, kSms);
+        const uint32_t ctas = (uint32_t)std::min<uint64_t>(items, (uint64_t)device_sms());
         const bool two = 2 * tab + tiles <= kPassSmem;
         const size_t smem = (two ? 2 : 1) * tab + tiles;
         if (lg_cw >= kSplitLgCw) {
@@ -1312,7 +1311,7 @@ cudaError_t pass_impl(const PassArgs &a, cudaStream_t s)
     }
     // About 4 tiles per CTA and at least ~6 CTAs per SM in total.
     size_t y = (ntiles + 3) / 4;
-    const size_t want = (kSms * 6 + ngroups - 1) / ngroups;
+    const size_t want = ((size_t)device_sms() * 6 + ngroups - 1) / ngroups;
     if (y < want) y = want;
     if (y > ntiles) y = ntiles;
     if (y < 1) y = 1;
@@ -1510,13 +1509,29 @@ cudaError_t launch_pointwise(int r, uint8_t *c, const uint8_t *t, size_t bytes, 
                              cudaStream_t s, uint64_t *launches)
 {
     const size_t words = bytes / 4;
-    const unsigned blocks = (unsigned)std::min<size_t>((words + kThreads - 1) / kThreads, (size_t)kSms * 16);
+    const unsigned blocks = (unsigned)std::min<size_t>((words + kThreads - 1) / kThreads, (size_t)device_sms() * 16);
     if (r == 8)
         k_pointwise<8><<<blocks, kThreads, 0, s>>>(c, t, bytes, tab.logt, tab.expt);
     else
         k_pointwise<16><<<blocks, kThreads, 0, s>>>(c, t, bytes, tab.logt, tab.expt);
     *launches += 1;
     return cudaGetLastError();
+}
+
+int device_sms()
+{
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev < kMaxDev) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    if (dev < kMaxDev) cache[dev].store(sms, std::memory_order_relaxed);
+    return sms;
 }
 
 cudaError_t configure_transform_kernels()
@@ -1618,7 +1633,7 @@ cudaError_t launch_broadcast(uint8_t *dst, const uint8_t *src, size_t S, uint32_
 {
     if (rows == 0) return cudaSuccess;
     const size_t total = S / 16 * rows;
-    const unsigned blocks = (unsigned)std::min<size_t>((total + kThreads - 1) / kThreads, (size_t)kSms * 16);
+    const unsigned blocks = (unsigned)std::min<size_t>((total + kThreads - 1) / kThreads, (size_t)device_sms() * 16);
     k_broadcast<<<blocks, kThreads, 0, s>>>(dst, src, S, rows);
     *launches += 1;
     return cudaGetLastError();
@@ -1645,7 +1660,7 @@ cudaError_t launch_rows_move(bool gather, uint8_t *dst, const uint8_t *src, cons
 {
     if (count == 0) return cudaSuccess;
     const size_t total = S / 16 * count;
-    const unsigned blocks = (unsigned)std::min<size_t>((total + kThreads - 1) / kThreads, (size_t)kSms * 16);
+    const unsigned blocks = (unsigned)std::min<size_t>((total + kThreads - 1) / kThreads, (size_t)device_sms() * 16);
     if (gather)
         k_rows_move<true><<<blocks, kThreads, 0, s>>>(dst, src, idx, count, S);
     else
@@ -1655,7 +1670,7 @@ cudaError_t launch_rows_move(bool gather, uint8_t *dst, const uint8_t *src, cons
 
 cudaError_t launch_fill(uint8_t *p, size_t bytes, cudaStream_t s)
 {
-    k_fill<<<kSms * 4, kThreads, 0, s>>>(reinterpret_cast<uint32_t *>(p), bytes / 4);
+    k_fill<<<device_sms() * 4, kThreads, 0, s>>>(reinterpret_cast<uint32_t *>(p), bytes / 4);
     return cudaGetLastError();
 }
 
@@ -1697,12 +1712,12 @@ cudaError_t deriv_impl(const DerivArgs &a, cudaStream_t s)
     const size_t ntiles_p = (a.S + (1ull << lg_cw) - 1) >> lg_cw;
     if (ntiles_p >= 2 && (uint64_t)ngroups * ntiles_p < (1ull << 32)) {
         const uint32_t items = (uint32_t)(ngroups * ntiles_p);
-        return launch_pdl(k_deriv_p<R, MODE>, dim3(std::min<uint32_t>(items, kSms)), dim3(kPassThreads), smem, s, a,
+        return launch_pdl(k_deriv_p<R, MODE>, dim3(std::min<uint32_t>(items, (uint32_t)device_sms())), dim3(kPassThreads), smem, s, a,
                           lg_cw, (uint32_t)ntiles_p, items);
     }
     const size_t ntiles = (a.S + (1ull << lg_cw) - 1) >> lg_cw;
     size_t y = (ntiles + 7) / 8;
-    const size_t want = (kSms * 6 + ngroups - 1) / ngroups;
+    const size_t want = ((size_t)device_sms() * 6 + ngroups - 1) / ngroups;
     if (y < want) y = want;
     if (y > ntiles) y = ntiles;
     if (y < 1) y = 1;

@@ -583,7 +583,7 @@ size_t batch_task_bytes(const lch_codeword *cws, uint32_t count)
 {
     uint64_t total = 0;
     for (uint32_t c = 0; c < count; c++) total += (uint64_t)cws[c].n * cws[c].shard_bytes;
-    const uint64_t want = total / (8ull * 152);
+    const uint64_t want = total / (8ull * (uint64_t)device_sms());
     return (size_t)std::min<uint64_t>(8ull << 20, std::max<uint64_t>(256ull << 10, want));
 }
 

@@ -219,6 +219,10 @@ void set_last_error(const char *msg);
 // Opt the large-shared-memory kernels in on the current device.
 cudaError_t configure_transform_kernels();
 
+// Streaming multiprocessors of the current device (queried once per device);
+// persistent grids take one CTA per SM and elementwise grids a multiple.
+int device_sms();
+
 // One transform pass: levels [L0, L0 + nlev) of an h-row transform, applied
 // to tiles of 2^nlev rows (row stride 2^L0) that are read from src and written
 // to dst (src == dst allowed).

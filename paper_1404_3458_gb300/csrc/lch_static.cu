@@ -122,6 +122,11 @@ extern "C" LCH_API int lch_derivative_noalloc(int field, uint32_t h, void *buf, 
     if (!is_pow2(h) || h > (1ull << field)) return fail(LCH_EINVAL, "h must be a power of two, at most 2^r");
     if (!buf || ((uintptr_t)buf & 15u)) return fail(LCH_EINVAL, "buffer must be non-NULL and 16-byte aligned");
     if (shard_bytes == 0 || (shard_bytes & 15u)) return fail(LCH_EINVAL, "shard_bytes must be a nonzero multiple of 16");
+    if (h == 1) { // a constant has derivative zero: no scratch, no tables
+        if (cudaMemsetAsync(buf, 0, shard_bytes, (cudaStream_t)stream) != cudaSuccess)
+            return fail(LCH_ECUDA, "cudaMemsetAsync failed");
+        return LCH_OK;
+    }
     if ((uint64_t)h * shard_bytes > kStaticScratchBytes)
         return fail(LCH_EINVAL, "h * shard_bytes exceeds the 16 MiB static scratch of lch_derivative_noalloc");
     int dev = 0;
@@ -133,10 +138,6 @@ extern "C" LCH_API int lch_derivative_noalloc(int field, uint32_t h, void *buf, 
     uint8_t *p = static_cast<uint8_t *>(buf);
     const size_t S = shard_bytes;
     uint64_t launches = 0;
-    if (h == 1) { // a constant has derivative zero
-        if (cudaMemsetAsync(p, 0, S, s) != cudaSuccess) return fail(LCH_ECUDA, "cudaMemsetAsync failed");
-        return LCH_OK;
-    }
     const uint16_t *B = st->btab + (field == LCH_GF16 ? 2 * 65536 : 0);
     const uint16_t *Binv = B + 65536;
     uint32_t lgh = 0;

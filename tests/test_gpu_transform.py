@@ -73,6 +73,21 @@ def test_derivative_matches_oracle(ctx, r, lgh, S):
     assert np.array_equal(got[:, cols], O.derivative(r, elems(host, r, cols)))
 
 
+@pytest.mark.parametrize("lgh,S", [(12, 4096), (13, 4112), (13, 8192)])
+def test_derivative_full_size_forms(ctx, lgh, S):
+    """Sec. IV.B at sizes where the derivative runs as two persistent passes
+    over the two bit groups (several column tiles per row group, ragged last
+    tile at S = 4112), against the oracle's monomial-basis derivative on
+    sampled element columns."""
+    r, h = 16, 1 << lgh
+    host = WL.shards(h, S, seed=4500 + lgh + S)
+    dev = to_dev(host)
+    ctx.derivative(r, dev)
+    cols = elem_cols(S, r, 6, seed=lgh + S)
+    got = elems(dev.cpu().numpy(), r, cols)
+    assert np.array_equal(got, O.derivative(r, elems(host, r, cols)))
+
+
 @pytest.mark.parametrize("lgh", list(range(8, 17)))
 def test_roundtrip_config2_sizes(ctx, lgh):
     """lch_fft / lch_ifft round trips at h = 2^8 .. 2^16 in GF(2^16) with

@@ -8,7 +8,8 @@ import ctypes
 import numpy as np
 import pytest
 
-from helpers import to_dev
+from helpers import elem_cols, elems, to_dev
+from oracle import oracle as O
 from paper_1404_3458_gb300 import build as B
 from paper_1404_3458_gb300 import lch
 from paper_1404_3458_gb300 import workloads as WL
@@ -41,3 +42,20 @@ def test_noalloc_matches_lch_derivative_on_consecutive_calls(ctx):
         lch.derivative_noalloc(r, got)
         torch.cuda.synchronize()
         assert np.array_equal(got.cpu().numpy(), ref.cpu().numpy()), (r, h, S)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("r,lgh,S", [(16, 12, 4096), (16, 13, 2048), (16, 13, 2032), (8, 8, 1040)])
+def test_noalloc_matches_oracle(ctx, r, lgh, S):
+    """The allocation-free derivative against the oracle's derivative
+    (Sec. IV.B, computed through the monomial basis) on sampled element
+    columns, at the sizes the 16 MiB scratch admits."""
+    import torch
+
+    h = 1 << lgh
+    host = WL.shards(h, S, seed=7100 + lgh + S)
+    got = to_dev(host)
+    lch.derivative_noalloc(r, got)
+    torch.cuda.synchronize()
+    cols = elem_cols(S, r, 6, seed=lgh + S)
+    assert np.array_equal(elems(got.cpu().numpy(), r, cols), O.derivative(r, elems(host, r, cols)))
