@@ -318,6 +318,22 @@ LCH_API int lch_tune_set(lch_ctx *ctx, int field, uint32_t h, size_t shard_bytes
  * e.g. to give other contexts the same plans; LCH_EINVAL when there is none. */
 LCH_API int lch_tune_get(lch_ctx *ctx, int field, uint32_t h, size_t shard_bytes, lch_tuning *plan);
 
+/* Arithmetic of the GF(2^16) transform passes (the paper has no counterpart;
+ * results are identical either way).  on == 0 (the default): every transform
+ * uses the split-table passes and the plans above.  on != 0: when
+ * shard_bytes is a multiple of 64, lch_fft, lch_ifft, lch_poly_mul and the
+ * transforms inside rs_encode / rs_decode run as bit-sliced passes: each
+ * 64-byte chunk of 32 elements is turned into 16 plane words, a product by a
+ * butterfly factor becomes plane XORs selected by the factor's bits, and the
+ * chunks are turned back when the transform's last pass stores them; the
+ * tuned plans do not apply to those transforms.  On a GB300 the bit-sliced
+ * passes are the slower of the two (about 1.3 against 1.9 T multiplies/s),
+ * which is why they are not the default.  Codewords whose whole decode or
+ * encode fits one tile (lg n <= 8, lg k <= 8), batches and GF(2^8) are not
+ * affected.  Not synchronised with work in flight.  LCH_EINVAL for a NULL
+ * ctx. */
+LCH_API int lch_set_bitslice(lch_ctx *ctx, int on);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,6 +29,9 @@ struct lch_ctx {
         int kind;
         uint64_t bytes, mults;
     };
+    // GF(2^16) transforms on shards of a multiple of 64 bytes run as
+    // bit-sliced passes (k_bitslice.cu) when this is set (lch_set_bitslice)
+    int bitslice = 0;
     bool prof_on = false;
     std::vector<Rec> prof;
     size_t prof_used = 0;
@@ -248,6 +251,72 @@ int run_pass(lch_ctx *ctx, int field, uint32_t h, uint32_t l, int inverse, const
     return LCH_OK;
 }
 
+// Bit-sliced transforms (GF(2^16), shards of a multiple of 64 bytes): lg h
+// levels in ceil(lg h / kBsMaxLev) passes, as even as possible, the low
+// passes taking the extra levels.  nl[] receives each pass's level count in
+// level order; returns the number of passes.
+uint32_t bs_split(uint32_t lgh, uint32_t nl[4])
+{
+    const uint32_t np = (lgh + kBsMaxLev - 1) / kBsMaxLev;
+    for (uint32_t k = 0; k < np; k++) nl[k] = lgh / np + (k < lgh % np ? 1u : 0u);
+    return np;
+}
+
+bool use_bitslice(const lch_ctx *ctx, int field, size_t S) { return field == LCH_GF16 && ctx->bitslice && S % 64 == 0; }
+
+// One bit-sliced pass over levels [L0, L0 + nlev) of an h-row transform with
+// shift l; g0 / ngroups / src_mask as in PassArgs (the coset passes of
+// Algorithm 1), rows counts the rows the pass writes.
+int run_bs_pass(lch_ctx *ctx, uint32_t h, uint32_t l, int inverse, const uint8_t *src, uint8_t *dst, size_t S,
+                uint32_t L0, uint32_t nlev, int in_std, int out_std, cudaStream_t s, uint32_t g0 = 0,
+                uint32_t ngroups = 0, uint32_t src_mask = 0xFFFFFFFFu)
+{
+    BsPassArgs p;
+    p.src = src;
+    p.dst = dst;
+    p.S = S;
+    p.h = h;
+    p.L0 = L0;
+    p.nlev = nlev;
+    p.l = l;
+    p.inverse = inverse;
+    p.fval = ctx->tab[1].fval;
+    p.in_std = in_std;
+    p.out_std = out_std;
+    p.g0 = g0;
+    p.ngroups = ngroups;
+    p.src_mask = src_mask;
+    const uint64_t rows = ngroups ? (uint64_t)ngroups << nlev : (uint64_t)h - ((uint64_t)g0 << nlev);
+    // multiplies executed: rows/2 per level, less the zero factors (shift 0:
+    // the butterflies whose block starts at row 0, 2^i at level i, Sec. III.D)
+    uint64_t mults = rows / 2 * nlev;
+    if (l == 0 && g0 == 0) mults -= (1ull << (L0 + nlev)) - (1ull << L0);
+    PROFM(LCH_KIND_PASS, 2 * rows * S, mults * (S / 2), launch_bs_pass(p, s, &ctx->launches));
+    return LCH_OK;
+}
+
+// h-point bit-sliced transform from src to dst; in_std / out_std: src / dst
+// in the standard layout (else sliced).
+int transform_bs(lch_ctx *ctx, uint32_t h, uint32_t l, int inverse, const uint8_t *src, uint8_t *dst, size_t S,
+                 cudaStream_t s, int in_std = 1, int out_std = 1)
+{
+    uint32_t nl[4], L0[4];
+    const uint32_t np = bs_split(lg2(h), nl);
+    for (uint32_t k = 0, acc = 0; k < np; k++) {
+        L0[k] = acc;
+        acc += nl[k];
+    }
+    int rc;
+    for (uint32_t i = 0; i < np; i++) {
+        const uint32_t k = inverse ? i : np - 1 - i; // Psi^-1: low levels first
+        const bool first = i == 0, last = i + 1 == np;
+        if ((rc = run_bs_pass(ctx, h, l, inverse, first ? src : dst, dst, S, L0[k], nl[k], first ? in_std : 0,
+                              last ? out_std : 0, s)))
+            return rc;
+    }
+    return LCH_OK;
+}
+
 // h-point transform (inverse != 0: (Psi_h^l)^-1) from src to dst.  Psi^-1
 // runs the low levels first, Psi the high levels first.
 int transform(lch_ctx *ctx, int field, uint32_t h, uint32_t l, int inverse, const uint8_t *src, uint8_t *dst,
@@ -258,6 +327,7 @@ int transform(lch_ctx *ctx, int field, uint32_t h, uint32_t l, int inverse, cons
         if (src != dst) CU(cudaMemcpyAsync(dst, src, S, cudaMemcpyDeviceToDevice, s), "copy");
         return LCH_OK;
     }
+    if (use_bitslice(ctx, field, S)) return transform_bs(ctx, h, l, inverse, src, dst, S, s);
     uint32_t a, b, lg[2];
     pass_plan(ctx, field, lgh, S, &a, &b, lg);
     int rc;
@@ -539,6 +609,26 @@ int encode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
     rc = ensure_scratch(ctx, (size_t)k * S);
     if (rc) return rc;
     uint8_t *mbar = ctx->scratch;
+    if (use_bitslice(ctx, field, S)) {
+        // bar M_k stays bit-sliced in scratch; the coset passes read it
+        // through the row mask, keep rows k..n-1 sliced between passes and
+        // write the standard layout in their last pass
+        if ((rc = transform_bs(ctx, k, 0, 1, shards, mbar, S, s, 1, 0))) return rc;
+        uint32_t nl[4], L0[4];
+        const uint32_t np = bs_split(lgk, nl);
+        for (uint32_t i = 0, acc = 0; i < np; i++) {
+            L0[i] = acc;
+            acc += nl[i];
+        }
+        for (uint32_t i = 0; i < np; i++) {
+            const uint32_t q = np - 1 - i; // Psi: high levels first
+            const uint32_t g0 = (k >> (L0[q] + nl[q])) << L0[q];
+            if ((rc = run_bs_pass(ctx, n, 0, 0, i == 0 ? mbar : shards, shards, S, L0[q], nl[q], 0, i + 1 == np, s,
+                                  g0, (n >> nl[q]) - g0, i == 0 ? k - 1 : 0xFFFFFFFFu)))
+                return rc;
+        }
+        return LCH_OK;
+    }
     // Algorithm 1 line 1: bar M_k = (Psi_k^0)^-1 [M_k]
     rc = transform(ctx, field, k, 0, 1, shards, mbar, S, s);
     if (rc) return rc;
@@ -965,6 +1055,7 @@ LCH_API int lch_ctx_create(lch_ctx **out, int device)
         DeviceScope ds(device);
         if (!ds.ok) return fail(LCH_ECUDA, "cannot select device %d", device);
         CU(configure_transform_kernels(), "configuring kernels");
+        CU(configure_bs_kernels(), "configuring kernels");
     }
     lch_ctx *ctx = new (std::nothrow) lch_ctx;
     if (!ctx) return fail(LCH_ENOMEM, "host allocation failed");
@@ -1364,6 +1455,13 @@ LCH_API int lch_tune_get(lch_ctx *ctx, int field, uint32_t h, size_t shard_bytes
     plan->lg_tile_low = it->second.lg[0];
     plan->lg_tile_high = it->second.lg[1];
     plan->ms = 0.f;
+    return LCH_OK;
+}
+
+LCH_API int lch_set_bitslice(lch_ctx *ctx, int on)
+{
+    if (!ctx) return fail(LCH_EINVAL, "ctx is NULL");
+    ctx->bitslice = on != 0;
     return LCH_OK;
 }
 

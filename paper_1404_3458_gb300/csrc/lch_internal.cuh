@@ -247,6 +247,27 @@ struct PassArgs {
 };
 cudaError_t launch_pass(int r, const PassArgs &a, cudaStream_t s, uint64_t *launches);
 
+// A pass of the bit-sliced GF(2^16) transform (k_bitslice.cu): as PassArgs,
+// with the factor values (fval) in place of their records, tiles of 2^nlev
+// rows x 2 KB (nlev <= kBsMaxLev) and shard bytes a multiple of 64.  in_std /
+// out_std: src / dst rows are in the standard layout (else bit-sliced).
+constexpr uint32_t kBsMaxLev = 6;
+struct BsPassArgs {
+    const uint8_t *src;
+    uint8_t *dst;
+    size_t S;
+    uint32_t h, L0, nlev, l;
+    int inverse;
+    const uint16_t *fval;
+    int in_std = 1, out_std = 1;
+    uint32_t g0 = 0;
+    uint32_t ngroups = 0;
+    uint32_t src_mask = 0xFFFFFFFFu;
+};
+bool bs_pass_ok(size_t S, uint32_t nlev);
+cudaError_t launch_bs_pass(const BsPassArgs &a, cudaStream_t s, uint64_t *launches);
+cudaError_t configure_bs_kernels();
+
 // Derivative helper: dst[t] (^)= XOR over l in [L0, L0+nlev) with bit l of t
 // clear of src[t + 2^l]   (one bit range of eq. XDhx3's inner sum).
 struct SupersetArgs {

@@ -98,6 +98,7 @@ def load() -> ctypes.CDLL:
         "lch_batch_selftest_stall": (i, [vp, vp]),
         "lch_tune_set": (i, [vp, i, u32, sz, ctypes.POINTER(Tuning)]),
         "lch_tune_get": (i, [vp, i, u32, sz, ctypes.POINTER(Tuning)]),
+        "lch_set_bitslice": (i, [vp, i]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -317,6 +318,11 @@ class Context:
         if load().lch_tune_get(self._h, field, h, shard_bytes, ctypes.byref(t)) != LCH_OK:
             return None
         return t.as_dict()
+
+    def set_bitslice(self, on: bool):
+        """lch_set_bitslice: GF(2^16) transforms as bit-sliced passes (True)
+        or split-table passes (False, the default); the results are the same."""
+        _check(load().lch_set_bitslice(self._h, int(bool(on))))
 
     # Sec. III: Psi_h^l and its inverse, in place on h rows.
     def fft(self, field: int, l: int, buf, stream=None):
