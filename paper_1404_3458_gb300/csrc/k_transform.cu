@@ -497,6 +497,99 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_p(PassArgs a, uint32_t
     pass_items<R, INV, RB, SPLIT>(a, lg_cw, ntiles, i0, i1, sm);
 }
 
+// Algorithm 1's middle two passes in one (n = 2k, one coset): the tile holds
+// 2^nlev rows of the k-row scratch that differ in the top bits [L0, lg k)
+// of the k-point transform.  It runs (Psi_k^0)^-1's levels L0 .. lg k - 1
+// (shift 0: the blocks at row 0 have factor 0), then the coset transform
+// Psi_k^k's levels lg k - 1 .. L0 on the same rows, and writes them to rows
+// k + row.  Every tile of such a top pass uses the same two factor sets
+// (hatW_i(w_j) and hatW_i(w_{k+j}) for the tile's blocks j), so both are
+// staged once per CTA: record set 0 for the inverse, set 1 for the coset.
+template <int R>
+__device__ __forceinline__ void fused_coset_tile(uint32_t sdata, uint32_t stab, uint32_t tab_sz, uint32_t nlev,
+                                                 uint32_t lg_w, const TileOut &o, const Lanes &ln)
+{
+    const uint32_t nrows = 1u << nlev, nrec = nrows - 1;
+    const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, qb = nlev - qa;
+    const uint32_t scos = stab + tab_sz;
+    if (qb) {
+        run_round<R, 1>(qa, sdata, stab, nrec, nrows, lg_w, 0, ln);
+        lanes_sync(ln);
+        run_round<R, 1, false, true>(qb, sdata, stab, nrec, nrows, lg_w, qa, ln);
+        lanes_sync(ln);
+        run_round<R, 0>(qb, sdata, scos, nrec, nrows, lg_w, qa, ln);
+        lanes_sync(ln);
+        run_round<R, 0, true>(qa, sdata, scos, nrec, nrows, lg_w, 0, ln, o);
+    } else {
+        run_round<R, 1, false, true>(qa, sdata, stab, nrec, nrows, lg_w, 0, ln);
+        lanes_sync(ln);
+        run_round<R, 0, true>(qa, sdata, scos, nrec, nrows, lg_w, 0, ln, o);
+    }
+}
+
+// Persistent form of the fused pass (as pass_items with one record buffer
+// that never changes hands, plus the coset's set).  a.h = k, a.l = 0,
+// a.L0 + a.nlev = lg k, a.src = the k-row scratch, a.dst = the codeword,
+// fuse_k = k.
+template <int R, bool SPLIT>
+__global__ void __launch_bounds__(kPassThreads, 1) k_pass_cos(PassArgs a, uint32_t lg_cw, uint32_t ntiles,
+                                                              uint32_t items, uint32_t fuse_k)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
+    const uint32_t i0 = (uint32_t)((uint64_t)blockIdx.x * items / gridDim.x);
+    const uint32_t i1 = (uint32_t)((uint64_t)(blockIdx.x + 1) * items / gridDim.x);
+    pdl_trigger();
+    const uint32_t nlev = a.nlev, nrows = 1u << nlev, nrec = nrows - 1;
+    const uint32_t tab_sz = tab_bytes<R>(nrec);
+    const uint32_t stab0 = (uint32_t)__cvta_generic_to_shared(sm);
+    const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
+    uint8_t *const buf0 = sm + 2 * tab_sz;
+    const uint32_t tile_bytes = nrows << lg_cw;
+    const uint32_t half = SPLIT ? threadIdx.x / (kPassThreads / 2) : 0u;
+    const Lanes ln = SPLIT ? Lanes{threadIdx.x % (kPassThreads / 2), kPassThreads / 2, half << (lg_w - 1), lg_w - 1, 1u + half}
+                           : lanes_all(lg_w);
+    const uint32_t lg_vh = SPLIT ? lg_vpr - 1 : lg_vpr, c0 = half << lg_vh;
+    auto issue = [&](uint32_t k, uint8_t *dstbuf) {
+        const uint32_t g = k / ntiles, t = k - (k / ntiles) * ntiles;
+        const size_t col = (size_t)t << lg_cw;
+        const size_t rem = a.S - col;
+        const uint32_t width = rem < cw ? (uint32_t)rem : cw;
+        for (uint32_t v = ln.tid; v < (nrows << lg_vh); v += ln.nthr) {
+            const uint32_t m = v >> lg_vh, c = c0 + (v & ((1u << lg_vh) - 1u));
+            if (c * 16 < width) {
+                const size_t row = ((size_t)m << a.L0) | g; // hibase = 0 in a top pass
+                cp_async16(dstbuf + (((m << lg_vpr) + c) << 4), a.src + row * a.S + col + c * 16);
+            }
+        }
+    };
+    if (i0 < i1) {
+        stage_pass_recs<R>(a, nrows, 0, sm);             // the inverse's factors
+        stage_pass_recs<R>(a, nrows, fuse_k, sm + tab_sz); // the coset's (rows k + j)
+    }
+    pdl_wait();
+    if (i0 < i1) issue(i0, buf0);
+    cp_async_commit();
+    for (uint32_t k = i0; k < i1; k++) {
+        uint8_t *data = buf0 + ((k - i0) & 1u) * tile_bytes;
+        uint8_t *next = buf0 + ((k + 1 - i0) & 1u) * tile_bytes;
+        const uint32_t sdata = (uint32_t)__cvta_generic_to_shared(data);
+        const uint32_t g = k / ntiles, t = k - (k / ntiles) * ntiles;
+        cp_async_wait_all();
+        if (!SPLIT || k == i0)
+            __syncthreads();
+        else
+            lanes_sync(ln);
+        if (k + 1 < i1) issue(k + 1, next);
+        cp_async_commit();
+        const size_t col = (size_t)t << lg_cw;
+        const size_t rem = a.S - col;
+        const TileOut o{a.dst, a.S, col, a.L0, fuse_k, g, rem < cw ? (uint32_t)rem : cw};
+        fused_coset_tile<R>(sdata, stab0, tab_sz, nlev, lg_w, o, ln);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kThreads) k_superset(SupersetArgs a, uint32_t lg_cw)
 {
     extern __shared__ __align__(128) uint8_t sm[];
@@ -1548,6 +1641,10 @@ cudaError_t configure_transform_kernels()
     if ((e = cudaFuncSetAttribute(k_deriv_p<16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv_p<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_deriv_p<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_cos<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_cos<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_cos<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_cos<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_pass_p<8, 0, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_pass_p<8, 0, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_pass_p<8, 0, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
@@ -1682,6 +1779,41 @@ cudaError_t launch_batch(const BatchOp *ops, const BatchTask *tasks, uint32_t nt
     k_batch<<<ctas, kPassThreads, batch_smem_bytes(), s>>>(ops, tasks, ntasks, counters, done, wait_ns);
     *launches += 1;
     return cudaGetLastError();
+}
+
+namespace {
+template <int R>
+cudaError_t pass_cos_impl(const PassArgs &a, uint32_t k, cudaStream_t s)
+{
+    const uint32_t nrows = 1u << a.nlev;
+    const size_t tab = tab_bytes<R>(nrows - 1);
+    uint32_t lg_cw = a.lg_cw ? a.lg_cw : pick_lg_cw(nrows, a.S);
+    while (lg_cw > 4 && 2 * tab + (2 * (size_t)nrows << lg_cw) > kPassSmem) lg_cw--;
+    const size_t smem = 2 * tab + (2 * (size_t)nrows << lg_cw);
+    if (smem > kPassSmem) return cudaErrorInvalidValue;
+    const uint32_t ngroups = k >> a.nlev;
+    const size_t ntiles = (a.S + (1ull << lg_cw) - 1) >> lg_cw;
+    const uint64_t items = (uint64_t)ngroups * ntiles;
+    if (items == 0 || items >= (1ull << 32)) return cudaErrorInvalidValue;
+    const uint32_t ctas = (uint32_t)std::min<uint64_t>(items, (uint64_t)device_sms());
+    if (lg_cw >= kSplitLgCw)
+        return launch_pdl(k_pass_cos<R, true>, dim3(ctas), dim3(kPassThreads), smem, s, a, lg_cw, (uint32_t)ntiles,
+                          (uint32_t)items, k);
+    return launch_pdl(k_pass_cos<R, false>, dim3(ctas), dim3(kPassThreads), smem, s, a, lg_cw, (uint32_t)ntiles,
+                      (uint32_t)items, k);
+}
+} // namespace
+
+bool pass_cos_fits(int r, uint32_t nlev)
+{
+    const size_t tab = r == 16 ? tab_bytes<16>((1u << nlev) - 1) : tab_bytes<8>((1u << nlev) - 1);
+    return nlev >= 1 && nlev <= 8 && 2 * tab + (2 * (size_t)(1u << nlev) << 4) <= kPassSmem;
+}
+
+cudaError_t launch_pass_coset(int r, const PassArgs &a, uint32_t k, cudaStream_t s, uint64_t *launches)
+{
+    *launches += 1;
+    return r == 8 ? pass_cos_impl<8>(a, k, s) : pass_cos_impl<16>(a, k, s);
 }
 
 cudaError_t launch_pass(int r, const PassArgs &a, cudaStream_t s, uint64_t *launches)

@@ -629,6 +629,50 @@ int encode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
         }
         return LCH_OK;
     }
+#ifndef LCH_NO_COSET_FUSION
+    if (n == 2 * k && lgk > 8 && pass_cos_fits(field, lgk - 8)) {
+        // One coset: line 1's high levels and line 3's high levels run as one
+        // pass over the same rows of bar M_k (k_pass_coset), so the middle of
+        // the encode reads the scratch once and writes the parity rows once.
+        // Low pass: 8 levels; the fused pass: the lg k - 8 levels above.
+        uint32_t a = 0, b = 0, lg[2] = {0, 0};
+        pass_plan(ctx, field, lgk, S, &a, &b, lg);
+        if (a != 8) lg[0] = lg[1] = 0;
+        const uint32_t hi = lgk - 8;
+        if ((rc = run_pass(ctx, field, k, 0, 1, shards, mbar, S, 0, 8, lg[0], s))) return rc;
+        PassArgs p;
+        p.src = mbar;
+        p.dst = shards;
+        p.S = S;
+        p.h = k;
+        p.L0 = 8;
+        p.nlev = hi;
+        p.l = 0;
+        p.inverse = 1;
+        p.rec = ctx->tab[field == LCH_GF16].rec;
+        p.lg_cw = lg[1];
+        // multiplies: the inverse's levels less the zero factors its top
+        // register round skips (as in run_pass), then the coset's levels
+        const uint32_t qa = hi <= 4 ? hi : (hi + 1) / 2, first = hi > qa ? 8 + qa : 8;
+        const uint64_t mults = (uint64_t)k / 2 * hi - ((1ull << lgk) - (1ull << first)) + (uint64_t)k / 2 * hi;
+        PROFM(LCH_KIND_PASS, 2ull * k * S, mults * cols, launch_pass_coset(field, p, k, s, &ctx->launches));
+        PassArgs q;
+        q.src = shards;
+        q.dst = shards;
+        q.S = S;
+        q.h = n;
+        q.L0 = 0;
+        q.nlev = 8;
+        q.l = 0;
+        q.inverse = 0;
+        q.rec = ctx->tab[field == LCH_GF16].rec;
+        q.lg_cw = lg[0];
+        q.g0 = k >> 8;
+        q.ngroups = (n >> 8) - q.g0;
+        PROFM(LCH_KIND_PASS, 2ull * k * S, (uint64_t)k / 2 * cols * 8, launch_pass(field, q, s, &ctx->launches));
+        return LCH_OK;
+    }
+#endif
     // Algorithm 1 line 1: bar M_k = (Psi_k^0)^-1 [M_k]
     rc = transform(ctx, field, k, 0, 1, shards, mbar, S, s);
     if (rc) return rc;

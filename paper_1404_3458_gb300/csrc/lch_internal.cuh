@@ -246,6 +246,13 @@ struct PassArgs {
     uint32_t src_mask = 0xFFFFFFFFu;
 };
 cudaError_t launch_pass(int r, const PassArgs &a, cudaStream_t s, uint64_t *launches);
+// Algorithm 1's two middle passes as one for n = 2k (k_pass_cos): levels
+// [L0, L0 + nlev) = [L0, lg k) of (Psi_k^0)^-1 on the k-row scratch a.src,
+// then the same levels of the coset transform Psi_k^k, written to rows
+// k .. 2k - 1 of the codeword a.dst (a.h = k, a.l = 0).  pass_cos_fits: the
+// two factor sets and two tiles of at least 16 bytes fit shared memory.
+bool pass_cos_fits(int r, uint32_t nlev);
+cudaError_t launch_pass_coset(int r, const PassArgs &a, uint32_t k, cudaStream_t s, uint64_t *launches);
 
 // A pass of the bit-sliced GF(2^16) transform (k_bitslice.cu): as PassArgs,
 // with the factor values (fval) in place of their records, tiles of 2^nlev

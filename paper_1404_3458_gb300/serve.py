@@ -105,8 +105,12 @@ def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
 
 def _estimate(r: Request) -> int:
     """Device bytes a request may need while in flight: its buffer, batch
-    scratch (at most 2 n S for a decode) and its share of the task queue."""
-    return 3 * r.n * r.shard_bytes + 16 * r.n + 65536
+    scratch (k S for the encode of Algorithm 1, at most 2 n S for a decode or
+    an encode with k not a power of two) and its share of the task queue."""
+    nS = r.n * r.shard_bytes
+    if r.op == lch.BATCH_ENCODE and r.k & (r.k - 1) == 0:
+        return nS + r.k * r.shard_bytes + 16 * r.n + 65536
+    return 3 * nS + 16 * r.n + 65536
 
 
 @dataclass
