@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-small", action="store_true", help="skip the small-workload latency lines")
     p.add_argument("--serve-requests", type=int, default=8192)
+    p.add_argument("--bitslice", action="store_true",
+                   help="run the GPU transforms as bit-sliced passes (lch_set_bitslice; slower than the default split-table passes)")
     return p.parse_args()
 
 
@@ -206,6 +208,7 @@ def run_ours(args):
     w = WL.WORKLOADS[args.workload]
     r, n, k, S = w.field, w.n, w.k, w.shard_bytes
     ctx = lch.Context(local)
+    ctx.set_bitslice(args.bitslice)
     stream = torch.cuda.current_stream()
     plans = {}
     if not args.no_tune:
@@ -317,7 +320,8 @@ def run_ours(args):
                    "erasures": ne, "erasure_pattern": "seeded uniform random",
                    "step": "rs_encode + rs_decode", "l2": "inputs larger than L2 (256 MiB codeword), no flush",
                    "parallelism": f"replicas x{world}",
-                   "pass_plans": plans or "default"},
+                   "pass_plans": plans or "default",
+                   "transform_passes": "bit-sliced" if args.bitslice else "split-table"},
         "hbm_roofline_step": {"alg_bytes_per_step": alg_bytes,
                               "achieved_gbs": round(alg_bytes / (step_ms / 1e3) / 1e9, 2),
                               "frac": round(alg_bytes / (step_ms / 1e3) / 1e9 / hbm, 4)},
