@@ -635,9 +635,17 @@ int encode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
         // pass over the same rows of bar M_k (k_pass_coset), so the middle of
         // the encode reads the scratch once and writes the parity rows once.
         // Low pass: 8 levels; the fused pass: the lg k - 8 levels above.
+        // tile widths: the k-point plan when its low pass has 8 levels, else
+        // the low pass of the n-point plan (an 8-level pass over the same
+        // shards), else the defaults
         uint32_t a = 0, b = 0, lg[2] = {0, 0};
         pass_plan(ctx, field, lgk, S, &a, &b, lg);
-        if (a != 8) lg[0] = lg[1] = 0;
+        if (a != 8) {
+            uint32_t lgn2[2] = {0, 0};
+            pass_plan(ctx, field, lgk + 1, S, &a, &b, lgn2);
+            lg[0] = a == 8 ? lgn2[0] : 0;
+            lg[1] = 0;
+        }
         const uint32_t hi = lgk - 8;
         if ((rc = run_pass(ctx, field, k, 0, 1, shards, mbar, S, 0, 8, lg[0], s))) return rc;
         PassArgs p;
