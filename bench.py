@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="large_gf16", choices=sorted(WL.WORKLOADS))
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--e2e-buffers", type=int, default=2, help="buffer sets the e2e pipeline rotates through")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--batch-count", type=int, default=4096)
@@ -630,7 +631,7 @@ def run_e2e(ctx, torch, host, mask, w, args):
     steps' kernels; each buffer is reused only after its last copy out.  The
     last step's outputs are checked against the true codeword."""
     r, n, k, S = w.field, w.n, w.k, w.shard_bytes
-    NB = 2
+    NB = args.e2e_buffers
     erased = np.nonzero(mask)[0]
     surv = np.nonzero(mask == 0)[0]
     ne, ns = erased.size, surv.size
