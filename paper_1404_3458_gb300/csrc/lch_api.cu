@@ -340,6 +340,99 @@ int transform(lch_ctx *ctx, int field, uint32_t h, uint32_t l, int inverse, cons
     return run_pass(ctx, field, h, l, 0, dst, dst, S, 0, a, lg[0], s);
 }
 
+// The row groups of an erasure pattern that a decode's two low-level passes
+// must touch (Sec. V, Algorithm 2).  Phi is zero on every erased row, and a
+// pass is linear, so a low pass of Psi^-1 (levels [0, a), groups of 2^a
+// consecutive rows) maps a group whose rows are all erased to zeros that are
+// already in place; the low pass of Psi (its last) only needs to produce the
+// erased rows, which the final division reads.  first[g] / last[g]: group g
+// of the inverse's / the transform's low pass is needed.
+void decode_groups(const MaskBits &bits, uint32_t n, uint32_t a, std::vector<uint8_t> &first,
+                   std::vector<uint8_t> &last)
+{
+    const uint32_t G = n >> a, rows = 1u << a;
+    first.assign(G, 0);
+    last.assign(G, 0);
+    for (uint32_t g = 0; g < G; g++) {
+        uint32_t ne = 0;
+        if (rows >= 32) {
+            for (uint32_t w = (g * rows) >> 5; w < ((g + 1) * rows) >> 5; w++) ne += (uint32_t)__builtin_popcount(bits.w[w]);
+        } else {
+            ne = (uint32_t)__builtin_popcount((bits.w[(g * rows) >> 5] >> ((g * rows) & 31u)) & ((1u << rows) - 1u));
+        }
+        first[g] = ne < rows;
+        last[g] = ne > 0;
+    }
+}
+
+// Maximal runs [g0, g1) of groups with keep[g] set.
+std::vector<std::pair<uint32_t, uint32_t>> group_runs(const std::vector<uint8_t> &keep)
+{
+    std::vector<std::pair<uint32_t, uint32_t>> runs;
+    for (uint32_t g = 0; g < keep.size();) {
+        if (!keep[g]) {
+            g++;
+            continue;
+        }
+        uint32_t e = g;
+        while (e < keep.size() && keep[e]) e++;
+        runs.emplace_back(g, e);
+        g = e;
+    }
+    return runs;
+}
+
+// A low pass (levels [0, nlev)) of an h-point transform over row groups
+// [g0, g0 + ngroups) only.
+int run_pass_groups(lch_ctx *ctx, int field, uint32_t h, int inverse, const uint8_t *src, uint8_t *dst, size_t S,
+                    uint32_t nlev, uint32_t lg_cw, uint32_t g0, uint32_t ngroups, cudaStream_t s)
+{
+    PassArgs p;
+    p.S = S;
+    p.h = h;
+    p.l = 0;
+    p.inverse = inverse;
+    p.rec = ctx->tab[field == LCH_GF16].rec;
+    p.src = src;
+    p.dst = dst;
+    p.L0 = 0;
+    p.nlev = nlev;
+    p.lg_cw = lg_cw;
+    p.g0 = g0;
+    p.ngroups = ngroups;
+    const uint64_t rows = (uint64_t)ngroups << nlev, cols = S / (field / 8);
+    PROFM(LCH_KIND_PASS, 2 * rows * S, rows / 2 * nlev * cols, launch_pass(field, p, s, &ctx->launches));
+    return LCH_OK;
+}
+
+// The decoder's n-point transforms in place on buf (shift 0), with the low
+// pass restricted to the groups `keep` marks (decode_groups) when they form
+// at most a few runs; otherwise, or with bit-sliced passes, the whole
+// transform.  keep_for is the low-pass level count keep was made for.
+int transform_decode(lch_ctx *ctx, int field, uint32_t h, int inverse, uint8_t *buf, size_t S,
+                     const std::vector<uint8_t> &keep, uint32_t keep_for, cudaStream_t s)
+{
+    const uint32_t lgh = lg2(h);
+    uint32_t a, b, lg[2];
+    pass_plan(ctx, field, lgh, S, &a, &b, lg);
+    const auto runs = group_runs(keep);
+    const bool prune = !use_bitslice(ctx, field, S) && b > 0 && a == keep_for && runs.size() <= 4 &&
+                       !(runs.size() == 1 && runs[0].first == 0 && runs[0].second == keep.size());
+    if (!prune) return transform(ctx, field, h, 0, inverse, buf, buf, S, s);
+    int rc;
+    if (inverse) {
+        for (const auto &r : runs)
+            if ((rc = run_pass_groups(ctx, field, h, 1, buf, buf, S, a, lg[0], r.first, r.second - r.first, s)))
+                return rc;
+        return run_pass(ctx, field, h, 0, 1, buf, buf, S, a, b, lg[1], s);
+    }
+    if ((rc = run_pass(ctx, field, h, 0, 0, buf, buf, S, a, b, lg[1], s))) return rc;
+    for (const auto &r : runs)
+        if ((rc = run_pass_groups(ctx, field, h, 0, buf, buf, S, a, lg[0], r.first, r.second - r.first, s)))
+            return rc;
+    return LCH_OK;
+}
+
 // Candidate level splits of an autotuned lg h-level transform: every listed
 // split whose two passes both have 1..8 levels (one pass when lg h <= 8).
 int tune_splits(uint32_t lgh, uint32_t out[4])
@@ -561,14 +654,21 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
     pk.mode = packed ? 1 : 0;
     PROFM(LCH_KIND_ROWSCALE, (uint64_t)(n - ne) * S + (uint64_t)n * S, (uint64_t)(n - ne) * cols,
           launch_rowscale(field, phi, packed ? received : shards, S, n, pre, 0, s, &ctx->launches, pk));
+    // The low passes of steps 3 and 5 skip the row groups they need not
+    // touch (decode_groups): whole groups of erased rows in step 3, groups
+    // without erased rows in step 5.
+    uint32_t pa, pb, plg[2];
+    pass_plan(ctx, field, lgn, S, &pa, &pb, plg);
+    std::vector<uint8_t> keep_first, keep_last;
+    if (pb) decode_groups(bits, n, pa, keep_first, keep_last);
     // Step 3: coefficients of hatF.
-    rc = transform(ctx, field, n, 0, 1, phi, phi, S, s);
+    rc = pb ? transform_decode(ctx, field, n, 1, phi, S, keep_first, pa, s) : transform(ctx, field, n, 0, 1, phi, phi, S, s);
     if (rc) return rc;
     // Step 4: formal derivative.
     rc = derivative(ctx, field, n, phi, phi2, phi2, S, s);
     if (rc) return rc;
     // Step 5: evaluate hatF'.
-    rc = transform(ctx, field, n, 0, 0, phi2, phi2, S, s);
+    rc = pb ? transform_decode(ctx, field, n, 0, phi2, S, keep_last, pa, s) : transform(ctx, field, n, 0, 0, phi2, phi2, S, s);
     if (rc) return rc;
     // Step 6: F(j) = hatF'(j) / Pi'(j), written to the erased rows only.
     PROFM(LCH_KIND_ROWSCALE, 2ull * ne * S, (uint64_t)ne * cols,
@@ -765,18 +865,21 @@ struct Planner {
     {
         add_tasks(stage, add_op(op), cw, groups, group_bytes);
     }
-    void add_tasks(uint32_t stage, uint32_t op, uint32_t cw, uint32_t units, size_t unit_bytes)
+    void add_tasks(uint32_t stage, uint32_t op, uint32_t cw, uint32_t units, size_t unit_bytes, uint32_t u0 = 0)
     {
         const uint32_t per = (uint32_t)std::max<size_t>(1, task_bytes / std::max<size_t>(1, unit_bytes));
-        for (uint32_t g = 0; g < units; g += per) {
+        for (uint32_t g = u0; g < units; g += per) {
             const uint32_t g1 = std::min(units, g + per);
             tasks.push_back({stage, op, cw, g, g1, (uint64_t)(g1 - g) * unit_bytes});
         }
     }
     // Transform passes of an h-point transform as in transform(); returns the
     // next free stage.  Tile widths are capped to the batch kernel's shared memory.
+    // keep (optional): the row groups of the low pass to run (decode_groups),
+    // made for a low pass of keep_for levels.
     uint32_t add_transform(uint32_t stage, uint32_t cw, int field, uint32_t h, uint32_t l, int inverse,
-                           const uint8_t *src, uint8_t *dst, size_t S)
+                           const uint8_t *src, uint8_t *dst, size_t S, const std::vector<uint8_t> *keep = nullptr,
+                           uint32_t keep_for = 0)
     {
         uint32_t a, b, lg[2];
         pass_plan(ctx, field, lg2(h), S, &a, &b, lg);
@@ -801,7 +904,12 @@ struct Planner {
             op.nlev = nl[p];
             op.l = l;
             op.tab0 = ctx->tab[field == LCH_GF16].rec;
-            add_group_tasks(stage + p, op, cw, h >> nl[p], ((size_t)1 << nl[p]) * S, S);
+            if (keep && b && L0[p] == 0 && nl[p] == keep_for) {
+                const uint32_t o = add_op(op);
+                for (const auto &r : group_runs(*keep)) add_tasks(stage + p, o, cw, r.second, ((size_t)1 << nl[p]) * S, r.first);
+            } else {
+                add_group_tasks(stage + p, op, cw, h >> nl[p], ((size_t)1 << nl[p]) * S, S);
+            }
         }
         return stage + (b ? 2 : 1);
     }
@@ -847,7 +955,18 @@ void plan_decode(Planner &P, uint32_t cw, uint32_t n, int field, uint8_t *shards
     rows.coef = pre;
     rows.mode = 0;
     P.add_tasks(stage++, P.add_op(rows), cw, n, S);
-    stage = P.add_transform(stage, cw, field, n, 0, 1, phi, phi, S);
+    // the low passes skip the row groups they need not touch (decode_groups)
+    uint32_t pa, pb, plg[2];
+    pass_plan(P.ctx, field, lgn, S, &pa, &pb, plg);
+    std::vector<uint8_t> keep_first, keep_last;
+    if (pb) {
+        MaskBits mb;
+        memset(&mb, 0, sizeof(mb));
+        for (uint32_t j = 0; j < n; j++)
+            if (mask[j]) mb.w[j >> 5] |= 1u << (j & 31);
+        decode_groups(mb, n, pa, keep_first, keep_last);
+    }
+    stage = P.add_transform(stage, cw, field, n, 0, 1, phi, phi, S, pb ? &keep_first : nullptr, pa);
     uint32_t a, b;
     split_levels(lgn, &a, &b);
     BatchOp d{};
@@ -880,7 +999,7 @@ void plan_decode(Planner &P, uint32_t cw, uint32_t n, int field, uint8_t *shards
         d.lg_cw = plan_deriv_lg_cw(field, b, 1, S, true);
         P.add_group_tasks(stage++, d, cw, n >> b, ((size_t)1 << b) * S, S);
     }
-    stage = P.add_transform(stage, cw, field, n, 0, 0, phi2, phi2, S);
+    stage = P.add_transform(stage, cw, field, n, 0, 0, phi2, phi2, S, pb ? &keep_last : nullptr, pa);
     rows.src = phi2;
     rows.dst = shards;
     rows.coef = post;

@@ -277,3 +277,71 @@ def test_rows_gather_scatter_round_trip():
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), cw[eras])
     c.close()
+
+
+def _pattern(n, kind):
+    """Erasure patterns that make a decode's low passes skip row groups:
+    aligned and unaligned bursts, erasures in two runs of groups, and one
+    group in four wholly erased (more runs than the skipping handles)."""
+    m = np.zeros(n, dtype=np.uint8)
+    if kind == "burst_aligned":
+        m[n // 4:3 * n // 4] = 1
+    elif kind == "burst_unaligned":
+        m[100:100 + n // 2] = 1
+    elif kind == "two_runs":
+        m[:64] = 1
+        m[n // 2:n // 2 + 64] = 1
+    elif kind == "scattered_groups":
+        for g in range(0, n // 64, 4):
+            m[g * 64:(g + 1) * 64] = 1
+    elif kind == "tail":
+        m[3 * n // 4:] = 1
+    return m
+
+
+@pytest.mark.parametrize("n,S", [(4096, 128), (65536, 64)])
+@pytest.mark.parametrize("kind", ["burst_aligned", "burst_unaligned", "two_runs", "scattered_groups", "tail"])
+def test_decode_with_skipped_row_groups(ctx, n, S, kind):
+    """Algorithm 2 with the low transform passes restricted to the row groups
+    they must touch: every byte of the codeword comes back, alone and (for
+    n <= 8192) in a batch, whose planner skips the same groups."""
+    import torch
+
+    r, k = 16, n // 2
+    cw = gpu_encode(ctx, r, n, k, message(n, k, S, seed=n + len(kind)))
+    mask = _pattern(n, kind)
+    assert 0 < mask.sum() <= n - k
+    assert np.array_equal(gpu_decode(ctx, r, n, k, cw, mask), cw)
+    if n > 8192:
+        return  # batches take n <= 2^13
+    bad = cw.copy()
+    bad[mask != 0] = 0x77
+    dev = to_dev(bad)
+    b = ctx.batch(lch.BATCH_DECODE, [(n, k, r, dev, mask)])
+    b.run()
+    b.status()
+    b.close()
+    torch.cuda.synchronize()
+    assert np.array_equal(dev.cpu().numpy(), cw)
+
+
+@pytest.mark.parametrize("n,k,S", [(4096, 3072, 80), (8192, 5000, 32)])
+def test_shortened_encode_with_skipped_groups(ctx, n, k, S):
+    """k not a power of two: the parity rows are the erasures {k..n-1}, a tail
+    burst, so the decoder's low passes skip most groups; the parity must still
+    be the oracle's interpolant on sampled columns, alone and in a batch."""
+    import torch
+
+    host = message(n, k, S, seed=n + k)
+    got = gpu_encode(ctx, 16, n, k, host)
+    cols = elem_cols(S, 16, 3, seed=k)
+    rows = np.sort(np.random.default_rng(k).choice(np.arange(k, n), 40, replace=False))
+    want = O.rs_encode(16, n, k, elems(host, 16, cols), rows=rows)
+    assert np.array_equal(elems(got, 16, cols)[rows], want[rows])
+    dev = to_dev(host)
+    b = ctx.batch(lch.BATCH_ENCODE, [(n, k, 16, dev, None)])
+    b.run()
+    b.status()
+    b.close()
+    torch.cuda.synchronize()
+    assert np.array_equal(dev.cpu().numpy(), got)
