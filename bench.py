@@ -325,7 +325,15 @@ def run_ours(args):
                    "transform_passes": "bit-sliced" if args.bitslice else "split-table"},
         "hbm_roofline_step": {"alg_bytes_per_step": alg_bytes,
                               "achieved_gbs": round(alg_bytes / (step_ms / 1e3) / 1e9, 2),
-                              "frac": round(alg_bytes / (step_ms / 1e3) / 1e9 / hbm, 4)},
+                              "frac": round(alg_bytes / (step_ms / 1e3) / 1e9 / hbm, 4),
+                              # what the step's kernels read and write (each kernel's declared bytes,
+                              # scratch round trips included; ncu finds 0.9-0.96 of them in DRAM)
+                              "kernel_bytes_per_step": int(sum(v["bytes"] for v in kinds.values()) / args.steps),
+                              "kernel_bytes_over_alg": round(sum(v["bytes"] for v in kinds.values()) / args.steps
+                                                             / alg_bytes, 2),
+                              "full_buffer_kernels": ("encode 3 transform passes; decode 7 (row scaling, 4 "
+                                                      "transform passes, 2 derivative passes) plus the division "
+                                                      "on the erased rows")},
         "latency_ms": {"encode_p50": round(pct(enc_ms, 50), 4), "encode_p99": round(pct(enc_ms, 99), 4),
                        "decode_p50": round(pct(dec_ms, 50), 4), "decode_p99": round(pct(dec_ms, 99), 4)},
         "kernels": {kk: {"launches": v["launches"], "ms": round(v["ms"], 4),
