@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--workload", default="large_gf16", choices=sorted(WL.WORKLOADS))
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-buffers", type=int, default=2, help="buffer sets the e2e pipeline rotates through")
+    p.add_argument("--e2e-copy-streams", type=int, default=1, help="streams each e2e copy is split over, per direction")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--batch-count", type=int, default=4096)
@@ -634,10 +635,12 @@ def run_e2e(ctx, torch, host, mask, w, args):
     parity out; then it copies in the surviving shards (packed, in row order),
     decodes them with rs_decode_packed, which writes the recovered shards
     packed in row order, and copies those out.  Steps are pipelined over NB
-    buffer sets and three streams (host-to-device copies, compute,
-    device-to-host copies), so one step's copies overlap the neighbouring
-    steps' kernels; each buffer is reused only after its last copy out.  The
-    last step's outputs are checked against the true codeword."""
+    buffer sets and three groups of streams (host-to-device copies, compute,
+    device-to-host copies; each copy split in row chunks over
+    --e2e-copy-streams streams per direction, so that several copy engines
+    share it), so one step's copies overlap the neighbouring steps' kernels;
+    each buffer is reused only after its last copy out.  The last step's
+    outputs are checked against the true codeword."""
     r, n, k, S = w.field, w.n, w.k, w.shard_bytes
     NB = args.e2e_buffers
     erased = np.nonzero(mask)[0]
@@ -654,70 +657,82 @@ def run_e2e(ctx, torch, host, mask, w, args):
     enc = [torch.empty((n, S), dtype=torch.uint8, device="cuda") for _ in range(NB)]
     pin_dev = [torch.empty((ns, S), dtype=torch.uint8, device="cuda") for _ in range(NB)]
     pout_dev = [torch.empty((ne, S), dtype=torch.uint8, device="cuda") for _ in range(NB)]
-    h2d, comp, d2h = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-    freed_e, freed_d = [None] * NB, [None] * NB  # slot's last copy out has finished
+    C = max(1, args.e2e_copy_streams)
+    h2d = [torch.cuda.Stream() for _ in range(C)]
+    d2h = [torch.cuda.Stream() for _ in range(C)]
+    comp = torch.cuda.Stream()
+    freed_e, freed_d = [[] for _ in range(NB)], [[] for _ in range(NB)]  # slot's last copies out
+
+    def copy_split(streams, dst, src, waits):
+        """dst <- src in len(streams) row chunks, one per stream, each after
+        the events in waits; returns the chunks' completion events."""
+        done = []
+        rows = src.shape[0]
+        per = (rows + len(streams) - 1) // len(streams)
+        for c, st in enumerate(streams):
+            r0, r1 = c * per, min(rows, (c + 1) * per)
+            if r0 >= r1:
+                continue
+            for e in waits:
+                st.wait_event(e)
+            with torch.cuda.stream(st):
+                dst[r0:r1].copy_(src[r0:r1], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(st)
+            done.append(ev)
+        return done
 
     def step(i, compute=True):
         b = i % NB
-        ev = [torch.cuda.Event() for _ in range(4)]
-        with torch.cuda.stream(h2d):
-            if freed_e[b] is not None:
-                h2d.wait_event(freed_e[b])
-            enc[b][:k].copy_(msg, non_blocking=True)           # message in
-            ev[0].record(h2d)
-            if freed_d[b] is not None:
-                h2d.wait_event(freed_d[b])
-            pin_dev[b].copy_(surv_host, non_blocking=True)     # surviving shards in
-            ev[1].record(h2d)
-        comp.wait_event(ev[0])
+        msg_in = copy_split(h2d, enc[b][:k], msg, freed_e[b])              # message in
+        surv_in = copy_split(h2d, pin_dev[b], surv_host, freed_d[b])       # surviving shards in
+        for e in msg_in:
+            comp.wait_event(e)
         if compute:
             ctx.rs_encode(n, k, r, enc[b], stream=comp)
-        ev[2].record(comp)
-        comp.wait_event(ev[1])
+        enc_done = torch.cuda.Event()
+        enc_done.record(comp)
+        for e in surv_in:
+            comp.wait_event(e)
         if compute:
             ctx.rs_decode_packed(n, k, r, pin_dev[b], pout_dev[b], mask, stream=comp)
-        ev[3].record(comp)
-        with torch.cuda.stream(d2h):
-            d2h.wait_event(ev[2])
-            parity_out[b].copy_(enc[b][k:], non_blocking=True)  # parity out
-            fe = torch.cuda.Event()
-            fe.record(d2h)
-            freed_e[b] = fe
-            d2h.wait_event(ev[3])
-            rec_out[b].copy_(pout_dev[b], non_blocking=True)    # recovered shards out
-            fd = torch.cuda.Event()
-            fd.record(d2h)
-            freed_d[b] = fd
+        dec_done = torch.cuda.Event()
+        dec_done.record(comp)
+        freed_e[b] = copy_split(d2h, parity_out[b], enc[b][k:], [enc_done])  # parity out
+        freed_d[b] = copy_split(d2h, rec_out[b], pout_dev[b], [dec_done])    # recovered shards out
+
+    def timed(compute):
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        start.record(h2d[0])
+        for st in h2d[1:]:
+            st.wait_event(start)
+        for i in range(steps):
+            step(i, compute)
+        for st in d2h[1:]:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            d2h[0].wait_event(ev)
+        stop.record(d2h[0])
+        torch.cuda.synchronize()
+        return start.elapsed_time(stop) / steps
 
     for i in range(max(3, args.warmup)):
         step(i)
     torch.cuda.synchronize()
     steps = max(4, args.steps // 2)
-    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(h2d)
-    for i in range(steps):
-        step(i)
-    z.record(d2h)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(z) / steps
+    ms = timed(True)
     last = (steps - 1) % NB
     ok = bool(torch.equal(rec_out[last], truth[torch.from_numpy(erased).long()])) and \
         bool(torch.equal(parity_out[last], truth[k:]))
     # the same schedule with the kernels left out: what the host link alone
     # takes for the step's copies (their bytes and stream order unchanged)
-    a2, z2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    a2.record(h2d)
-    for i in range(steps):
-        step(i, compute=False)
-    z2.record(d2h)
-    torch.cuda.synchronize()
-    copy_ms = a2.elapsed_time(z2) / steps
+    copy_ms = timed(False)
     return {"value": round((k + ne) * S / (ms / 1e3) / 1e9, 3), "unit": UNIT,
             "h2d_bytes_per_step": (k + ns) * S, "d2h_bytes_per_step": (n - k + ne) * S,
             "ms_per_step": round(ms, 4), "copy_only_ms_per_step": round(copy_ms, 4),
             "copy_gbs_each_way": round(((k + ns) * S + (n - k + ne) * S) / 2 / (copy_ms / 1e3) / 1e9, 2),
-            "pipelined": f"{NB} buffer sets, 3 streams",
+            "pipelined": f"{NB} buffer sets; each copy split over {C} stream(s) per direction, one compute stream",
             "received": "surviving shards only (packed); recovered shards packed (rs_decode_packed)",
             "verified": ok}
 
