@@ -765,14 +765,15 @@ def host_cpu():
 
 
 def _oracle_job(job):
-    """One single-threaded timing job in a worker process.
+    """One timing job in a worker process (single-threaded).
 
-    ("enc" | "dec", rows, seed, workload): one oracle rs_encode / rs_decode
-    call of the workload over all element columns, evaluating `rows` parity
-    (or erased) rows; rows = 0 evaluates none, so the call is only the
-    barycentric weights over the k interpolation points (O(k^2), paid once
-    per call).  ("fast", 0, seed, workload): one encode and one decode of the
-    whole workload by the O(n lg n) CPU restatement.  Returns seconds."""
+    ("enc" | "dec", rows, seed, workload): two oracle rs_encode / rs_decode
+    calls of the workload over all element columns, back to back in this
+    process: one evaluating no rows (only the barycentric weights over the k
+    interpolation points, O(k^2), which every call pays once) and one
+    evaluating `rows` parity (or erased) rows.  Returns (weights s, call s).
+    ("fast", 0, seed, workload): one encode and one decode of the whole
+    workload by the O(n lg n) CPU restatement; returns (encode s, decode s)."""
     kind, nrows, seed, wname = job
     w = WL.WORKLOADS[wname]
     r, n, k, S = w.field, w.n, w.k, w.shard_bytes
@@ -795,13 +796,16 @@ def _oracle_job(job):
         return (t1 - t0, t2 - t1)
     O.gf_mul(r, 1, 1)  # library loaded before timing
     pool = np.arange(k, n) if kind == "enc" else np.nonzero(mask)[0]
-    rows = np.sort(g.choice(pool, nrows, replace=False)).astype(np.int32) if nrows else np.zeros(0, np.int32)
-    t0 = time.perf_counter()
-    if kind == "enc":
-        O.rs_encode(r, n, k, el, rows=rows)
-    else:
-        O.rs_decode(r, n, k, el, mask, rows=rows)
-    return time.perf_counter() - t0
+    rows = np.sort(g.choice(pool, nrows, replace=False)).astype(np.int32)
+    out = []
+    for sel in (np.zeros(0, np.int32), rows):
+        t0 = time.perf_counter()
+        if kind == "enc":
+            O.rs_encode(r, n, k, el, rows=sel)
+        else:
+            O.rs_decode(r, n, k, el, mask, rows=sel)
+        out.append(time.perf_counter() - t0)
+    return tuple(out)
 
 
 def _run_jobs(jobs, workers):
@@ -826,16 +830,16 @@ def oracle_extrapolate(w, rows, t_wenc, t_wdec, t_enc, t_dec):
     return step_s, per_enc, per_dec
 
 
-def cpu_baseline(w, rows=64):
-    """The oracle's whole-step time, extrapolated (see oracle_extrapolate), and
-    the O(n lg n) CPU restatement's measured whole step, each one core.  The
-    four single-threaded oracle calls run side by side in four processes; the
-    O(n lg n) step runs alone after them (it is memory-bound, and running
-    beside the others slowed it by about half)."""
+def cpu_baseline(w, rows=128):
+    """The oracle's whole-step time, extrapolated (see oracle_extrapolate)
+    from an encode and a decode job run side by side (each times its
+    weights-only call and its sampled call back to back), and the O(n lg n)
+    CPU restatement's measured whole step, each on one core.  The O(n lg n)
+    step runs alone after them (it is memory-bound, and running beside the
+    others slowed it by about half)."""
     rows = min(rows, w.n - w.k, w.erasures)
-    jobs = [("enc", 0, 1, w.name), ("enc", rows, 1, w.name), ("dec", 0, 2, w.name), ("dec", rows, 2, w.name)]
     t0 = time.perf_counter()
-    twe, te, twd, td = _run_jobs(jobs, len(jobs))
+    (twe, te), (twd, td) = _run_jobs([("enc", rows, 1, w.name), ("dec", rows, 2, w.name)], 2)
     wall = time.perf_counter() - t0
     fe, fd = _run_jobs([("fast", 0, 3, w.name)], 1)[0]
     step_s, pe, pd = oracle_extrapolate(w, rows, twe, twd, te, td)
@@ -844,11 +848,11 @@ def cpu_baseline(w, rows=64):
     return {"value": round(data / step_s / 1e9, 9), "unit": UNIT, "cores": 1, "kind": "oracle",
             "extrapolated": True, "host_cpu": cpu,
             "sample": (f"oracle rs_encode and rs_decode of {w.name} over all {w.shard_bytes // (w.field // 8)} "
-                       f"element columns: one call each evaluating {rows} rows and one each evaluating none "
-                       f"(barycentric weights only: {twe:.2f} s / {twd:.2f} s); per row {pe * 1e3:.1f} ms "
-                       f"(encode) / {pd * 1e3:.1f} ms (decode); step extrapolated to {w.n - w.k} parity + "
-                       f"{w.erasures} erased rows = {step_s:.0f} s on one core; the 4 single-threaded calls "
-                       f"ran side by side ({wall:.1f} s wall)"),
+                       f"element columns: per operation, a call evaluating no rows (barycentric weights only: "
+                       f"{twe:.2f} s / {twd:.2f} s) and, right after it in the same process, a call evaluating "
+                       f"{rows} rows; per row {pe * 1e3:.1f} ms (encode) / {pd * 1e3:.1f} ms (decode); step "
+                       f"extrapolated to {w.n - w.k} parity + {w.erasures} erased rows = {step_s:.0f} s on one "
+                       f"core; the two processes ran side by side ({wall:.1f} s wall)"),
             "oracle_step_s_extrapolated": round(step_s, 1),
             "fast_onlgn": {"value": round(data / (fe + fd) / 1e9, 6), "unit": UNIT, "cores": 1,
                            "encode_s": round(fe, 3), "decode_s": round(fd, 3), "extrapolated": False,
@@ -859,49 +863,54 @@ def cpu_baseline(w, rows=64):
 
 def run_reference(args):
     """The reference arm: the oracle (the repository's plain-definition
-    checker) on the host cores.  A step is one oracle call over all element
-    columns evaluating a fixed sample of 32 rows (fewer if the code has fewer): an encode (even steps) or a
-    decode (odd steps).  Steps run side by side in a pool of worker processes,
-    one single-threaded call each.  Two further calls evaluate no rows (the
-    barycentric weights alone), so the per-row cost is the call time less the
-    weights; value = the step's shard data over the whole-step time
+    checker) on the host cores.  A step is one oracle job over all element
+    columns on a fixed sample of 64 rows (fewer if the code has fewer): an
+    encode on even steps, a decode on odd ones.  The job times a call that
+    evaluates no rows (the barycentric weights alone) and, right after it in
+    the same process, the call on the sample, so the per-row cost is their
+    difference; the step's value is its shard data over the whole step
     extrapolated from those (weights once per call, per-row cost times the
-    rows of a step)."""
+    rows of a step).  Steps run side by side in a pool of worker processes,
+    each single-threaded."""
     world, rank, _ = dist_setup(False)
     if rank != 0:
         return
     w = WL.WORKLOADS[args.workload]
     n, k, S = w.n, w.k, w.shard_bytes
     ne = w.erasures
-    rows = min(32, n - k, ne)
+    rows = min(64, n - k, ne)
     total = args.warmup + args.steps
-    workers = max(2, min(total + 2, (os.cpu_count() or 2) - 1, 16))
-    jobs = [("enc", 0, 0, w.name), ("dec", 0, 0, w.name)]
-    jobs += [("enc" if i % 2 == 0 else "dec", rows, 1000 + i, w.name) for i in range(total)]
+    workers = max(2, min(total, (os.cpu_count() or 2) - 1, 16))
+    jobs = [("enc" if i % 2 == 0 else "dec", rows, 1000 + i, w.name) for i in range(total)]
     t0 = time.perf_counter()
     res = _run_jobs(jobs, workers)
     wall = time.perf_counter() - t0
-    twe, twd = res[0], res[1]
-    timed = res[2 + args.warmup:]
+    timed = res[args.warmup:]
     kinds = ["enc" if i % 2 == 0 else "dec" for i in range(total)][args.warmup:]
-    te = [t for t, kd in zip(timed, kinds) if kd == "enc"] or [twe]
-    td = [t for t, kd in zip(timed, kinds) if kd == "dec"] or [twd]
-    step_s, pe, pd = oracle_extrapolate(w, rows, twe, twd, statistics.mean(te), statistics.mean(td))
+    enc = [x for x, kd in zip(timed, kinds) if kd == "enc"] or [res[0]]
+    dec = [x for x, kd in zip(timed, kinds) if kd == "dec"] or [res[1] if len(res) > 1 else res[0]]
+    # medians over the jobs: a job slowed by its neighbours moves neither
+    twe = statistics.median(x[0] for x in enc)
+    twd = statistics.median(x[0] for x in dec)
+    de = statistics.median(x[1] - x[0] for x in enc)
+    dd = statistics.median(x[1] - x[0] for x in dec)
+    step_s, pe, pd = oracle_extrapolate(w, rows, twe, twd, twe + de, twd + dd)
     value = (k + ne) * S / step_s / 1e9
     cpu = host_cpu()
-    sample = (f"per step: one oracle call over all {S // (w.field // 8)} element columns of {w.name} evaluating "
-              f"{rows} rows, an encode (even steps) or a decode (odd steps); two more calls evaluate no rows "
-              f"(weights only: {twe:.2f} / {twd:.2f} s); per row {pe * 1e3:.1f} / {pd * 1e3:.1f} ms; value = "
-              f"(k + |E|) S over the whole step extrapolated to {n - k} parity + {ne} erased rows "
-              f"({step_s:.0f} s on one core); {workers} single-threaded calls ran side by side "
+    sample = (f"per step: one oracle job over all {S // (w.field // 8)} element columns of {w.name}, an encode "
+              f"(even steps) or a decode (odd steps): a call evaluating no rows (weights only: median {twe:.2f} / "
+              f"{twd:.2f} s) and right after it a call evaluating {rows} rows; per row (median over the jobs) "
+              f"{pe * 1e3:.1f} / "
+              f"{pd * 1e3:.1f} ms; value = (k + |E|) S over the whole step extrapolated to {n - k} parity + {ne} "
+              f"erased rows ({step_s:.0f} s on one core); {workers} single-threaded jobs ran side by side "
               f"({wall:.0f} s wall)")
     out = {"metric": METRIC, "value": round(value, 9), "unit": UNIT, "impl": "reference", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": round(1e3 * statistics.mean(timed), 1) if timed else None,
+           "ms_per_step": round(1e3 * statistics.mean(x[0] + x[1] for x in timed), 1) if timed else None,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
            "data": "synthetic",
            "config": {"workload": w.name, "field": f"GF(2^{w.field})", "n": n, "k": k, "shard_bytes": S,
-                      "erasures": ne, "step": f"one oracle rs_encode or rs_decode call on a fixed {rows}-row sample"},
+                      "erasures": ne, "step": f"one oracle rs_encode or rs_decode job on a fixed {rows}-row sample"},
            "cpu_baseline": {"value": round(value, 9), "unit": UNIT, "cores": workers, "kind": "oracle",
                             "extrapolated": True, "host_cpu": cpu, "sample": sample},
            "e2e": {"value": round(value, 9), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
