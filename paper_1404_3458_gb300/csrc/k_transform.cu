@@ -1169,8 +1169,11 @@ __device__ __forceinline__ void tile_nbr_sums(uint32_t su, uint32_t sacc, uint32
 #undef LCH_NS
 }
 
-template <int R>
-__global__ void __launch_bounds__(kPassThreads, 1) k_fused_dec(FusedDecArgs a, uint32_t lg_cw)
+// NT threads: 1024 when a slice has at least 4096 words (32 warps hide the
+// barriers between the decode's many short phases better: medium_gf16 96 us
+// against 102 at 512), else 512.
+template <int R, int NT>
+__global__ void __launch_bounds__(NT, 1) k_fused_dec(FusedDecArgs a, uint32_t lg_cw)
 {
     extern __shared__ __align__(128) uint8_t sm[];
     constexpr uint32_t cpr = FT<R>::rec_bytes / 16;
@@ -1669,8 +1672,10 @@ cudaError_t configure_transform_kernels()
     if ((e = cudaFuncSetAttribute(k_deriv<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_fused_enc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_fused_enc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_fused_dec<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_fused_dec<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_fused_dec<8, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_fused_dec<16, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_fused_dec<8, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_fused_dec<16, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes())))
         return e;
     return cudaFuncSetAttribute(k_superset, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -1886,10 +1891,16 @@ cudaError_t launch_fused_decode(int r, const FieldTables &t, uint32_t lgn, uint8
     const FusedDecArgs a{shards, S, lgn, t.rec, t.brec, t.binvrec, pre, post, prerec, postrec};
     const dim3 grid((unsigned)((S + (1ull << lg_cw) - 1) >> lg_cw));
     cudaError_t e;
-    if (r == 8)
-        e = launch_pdl(k_fused_dec<8>, grid, dim3(kPassThreads), fused_dec_smem<8>(lgn, lg_cw), s, a, lg_cw);
-    else
-        e = launch_pdl(k_fused_dec<16>, grid, dim3(kPassThreads), fused_dec_smem<16>(lgn, lg_cw), s, a, lg_cw);
+    {
+        const bool wide = ((1u << lgn) << (lg_cw - 2)) >= 4096;
+        const size_t smem = r == 8 ? fused_dec_smem<8>(lgn, lg_cw) : fused_dec_smem<16>(lgn, lg_cw);
+        if (r == 8)
+            e = wide ? launch_pdl(k_fused_dec<8, 1024>, grid, dim3(1024), smem, s, a, lg_cw)
+                     : launch_pdl(k_fused_dec<8, 512>, grid, dim3(512), smem, s, a, lg_cw);
+        else
+            e = wide ? launch_pdl(k_fused_dec<16, 1024>, grid, dim3(1024), smem, s, a, lg_cw)
+                     : launch_pdl(k_fused_dec<16, 512>, grid, dim3(512), smem, s, a, lg_cw);
+    }
     *launches += 1;
     return e;
 }
