@@ -345,3 +345,20 @@ def test_shortened_encode_with_skipped_groups(ctx, n, k, S):
     b.close()
     torch.cuda.synchronize()
     assert np.array_equal(dev.cpu().numpy(), got)
+
+
+@pytest.mark.parametrize("lgk,S", [(9, 48), (10, 4112), (11, 64), (12, 2064), (13, 16), (14, 80)])
+def test_encode_one_coset_fused_middle(ctx, lgk, S):
+    """n = 2k with lg k > 8: Algorithm 1's two middle passes run as one
+    (the inverse's levels 8 .. lg k - 1, then the coset's), for every depth
+    of that fused pass from 1 to 6 levels; sampled parity rows against the
+    oracle's Lagrange evaluation, ragged column tiles included."""
+    k = 1 << lgk
+    n = 2 * k
+    host = message(n, k, S, seed=lgk + S)
+    got = gpu_encode(ctx, 16, n, k, host)
+    cols = elem_cols(S, 16, 4, seed=lgk)
+    rows = np.sort(np.random.default_rng(lgk).choice(np.arange(k, n), 32, replace=False))
+    want = O.rs_encode(16, n, k, elems(host, 16, cols), rows=rows)
+    assert np.array_equal(elems(got, 16, cols)[rows], want[rows])
+    assert np.array_equal(got[:k], host[:k])
