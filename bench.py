@@ -726,8 +726,9 @@ def run_e2e(ctx, torch, host, mask, w, args):
     ok = bool(torch.equal(rec_out[last], truth[torch.from_numpy(erased).long()])) and \
         bool(torch.equal(parity_out[last], truth[k:]))
     # the same schedule with the kernels left out: what the host link alone
-    # takes for the step's copies (their bytes and stream order unchanged)
-    copy_ms = timed(False)
+    # takes for the step's copies (their bytes and stream order unchanged);
+    # the better of two runs, as the link's speed varies with the host's load
+    copy_ms = min(timed(False), timed(False))
     return {"value": round((k + ne) * S / (ms / 1e3) / 1e9, 3), "unit": UNIT,
             "h2d_bytes_per_step": (k + ns) * S, "d2h_bytes_per_step": (n - k + ne) * S,
             "ms_per_step": round(ms, 4), "copy_only_ms_per_step": round(copy_ms, 4),
