@@ -621,12 +621,48 @@ def run_small_latency(ctx, torch, rank, warmup=10, reps=200):
         torch.cuda.synchronize()
         enc = [ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(reps)]
         dec = [ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(reps)]
+        graphed = graph_latency(ctx, torch, n, k, r, buf, mask, reps)
         res[name] = {"n": n, "k": k, "shard_bytes": S, "erasures": int(mask.sum()), "calls": reps,
+                     "graph_replay_ms_p50": graphed,
                      "encode_ms_p50": round(pct(enc, 50), 4), "encode_ms_p99": round(pct(enc, 99), 4),
                      "decode_ms_p50": round(pct(dec, 50), 4), "decode_ms_p99": round(pct(dec, 99), 4),
                      "encode_gbs_p50": round(k * S / (pct(enc, 50) / 1e3) / 1e9, 2),
                      "decode_gbs_p50": round(int(mask.sum()) * S / (pct(dec, 50) / 1e3) / 1e9, 2)}
     return res
+
+
+def graph_latency(ctx, torch, n, k, r, buf, mask, reps):
+    """Device-side latency of one encode and one decode: each call captured
+    in a CUDA graph and replayed `reps` times, CUDA events around every
+    replay.  Unlike the eager calls (whose events also enclose the Python
+    binding and the launches), the replay's kernels run back to back."""
+    out = {}
+    try:
+        for name, call in (("encode", lambda: ctx.rs_encode(n, k, r, buf)),
+                           ("decode", lambda: ctx.rs_decode(n, k, r, buf, mask))):
+            g = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                call()  # warm on the capture stream
+                with torch.cuda.graph(g, stream=side):
+                    call()
+            torch.cuda.current_stream().wait_stream(side)
+            for _ in range(10):
+                g.replay()
+            torch.cuda.synchronize()
+            st = torch.cuda.current_stream()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+            for i in range(reps):
+                ev[2 * i].record(st)
+                g.replay()
+                ev[2 * i + 1].record(st)
+            torch.cuda.synchronize()
+            out[name] = round(pct([ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(reps)], 50), 4)
+            del g
+    except Exception as e:  # report, do not fail the bench line
+        out["error"] = str(e)[:200]
+    return out
 
 
 def run_e2e(ctx, torch, host, mask, w, args):
