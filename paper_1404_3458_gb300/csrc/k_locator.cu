@@ -24,14 +24,15 @@ namespace lch {
 namespace {
 
 // MODE 0: FWHT(L) -> fl_out.  MODE 1: full locator -> pre/post.
-// MODE 1 with rec_pre / rec_post: also the split-table records of every
-// Pi(j) and 1/Pi'(j) (zero records for the other rows), in the region layout
-// of n records, for the fused short-codeword decode.
+// MODE 1 with rec_pp: also one set of split-table records, in the region
+// layout of n records, for the fused short-codeword decode: row j's record is
+// that of Pi(j) when j survives and of 1/Pi'(j) when j is erased (every row
+// needs exactly one of the two).
 template <int R, int MODE>
 __global__ void __launch_bounds__(1024) k_loc_small(uint32_t lgn, MaskBits bits, const uint16_t *__restrict__ logt,
                                                     const uint16_t *__restrict__ expt, const uint32_t *__restrict__ fl,
                                                     uint32_t *fl_out, uint16_t *pre, uint16_t *post, uint32_t ninv,
-                                                    uint8_t *rec_pre, uint8_t *rec_post)
+                                                    uint8_t *rec_pp)
 {
     extern __shared__ uint32_t v[];
     pdl_trigger();
@@ -46,18 +47,26 @@ __global__ void __launch_bounds__(1024) k_loc_small(uint32_t lgn, MaskBits bits,
         for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) v[j] = mmul<R>(v[j], fl[j]);
         __syncthreads();
         fwht_smem<R>(v, lgn);
-        for (uint32_t j = threadIdx.x; j < n; j += blockDim.x)
-            emit<R>(j, mmul<R>(v[j], ninv), mask_bit(bits, j), expt, pre, post);
-        if (rec_pre) {
+        if (rec_pp) {
+            // each row's constant once (its table lookups all in flight
+            // together), kept in v for the record chunks that follow
             constexpr uint32_t M = (1u << R) - 1, cpr = FT<R>::rec_bytes / 16;
+            for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
+                const uint32_t cj = mmul<R>(v[j], ninv);
+                const bool e = mask_bit(bits, j);
+                const uint32_t kp = e ? 0u : expt[cj], kd = e ? expt[cj == 0 ? 0 : M - cj] : 0u;
+                pre[j] = (uint16_t)kp;
+                post[j] = (uint16_t)kd;
+                v[j] = kp | kd;
+            }
+            __syncthreads();
             for (uint32_t i = threadIdx.x; i < n * cpr; i += blockDim.x) {
                 const uint32_t q = i / cpr, c = i - q * cpr;
-                const uint32_t cq = mmul<R>(v[q], ninv);
-                const bool e = mask_bit(bits, q);
-                const uint32_t kp = e ? 0u : expt[cq], kd = e ? expt[cq == 0 ? 0 : M - cq] : 0u;
-                *reinterpret_cast<uint4 *>(rec_pre + rec_dst<R>(n, q, c)) = rec_chunk<R>(kp, c);
-                *reinterpret_cast<uint4 *>(rec_post + rec_dst<R>(n, q, c)) = rec_chunk<R>(kd, c);
+                *reinterpret_cast<uint4 *>(rec_pp + rec_dst<R>(n, q, c)) = rec_chunk<R>(v[q], c);
             }
+        } else {
+            for (uint32_t j = threadIdx.x; j < n; j += blockDim.x)
+                emit<R>(j, mmul<R>(v[j], ninv), mask_bit(bits, j), expt, pre, post);
         }
     }
 }
@@ -126,7 +135,7 @@ constexpr uint32_t kSmallLg = 12;
 template <int R>
 cudaError_t run(int mode, const FieldTables &t, uint32_t lgn, const MaskBits *bits, const uint32_t *fl,
                 uint32_t *fl_out, uint32_t *work, uint16_t *pre, uint16_t *post, cudaStream_t s, uint64_t *launches,
-                uint8_t *rec_pre = nullptr, uint8_t *rec_post = nullptr)
+                uint8_t *rec_pp = nullptr)
 {
     constexpr uint32_t M = (1u << R) - 1;
     const uint32_t ninv = (uint32_t)((1ull << (R - lgn)) % M);
@@ -135,14 +144,15 @@ cudaError_t run(int mode, const FieldTables &t, uint32_t lgn, const MaskBits *bi
     cudaError_t e;
     if (lgn <= kSmallLg) {
         const uint32_t n = 1u << lgn;
-        const unsigned threads = n < 1024 ? (n < 32 ? 32 : n) : 1024;
+        // the record chunks (n x rec_bytes / 16 of them) want every thread
+        const unsigned threads = rec_pp ? 1024 : n < 1024 ? (n < 32 ? 32 : n) : 1024;
         const size_t smem = sizeof(uint32_t) * n;
         if (mode == 0)
             e = launch_pdl(k_loc_small<R, 0>, dim3(1), dim3(threads), smem, s, lgn, mb, t.logt, t.expt, fl, fl_out, pre, post, ninv,
-                           (uint8_t *)nullptr, (uint8_t *)nullptr);
+                           (uint8_t *)nullptr);
         else
             e = launch_pdl(k_loc_small<R, 1>, dim3(1), dim3(threads), smem, s, lgn, mb, t.logt, t.expt, fl, fl_out, pre, post, ninv,
-                           rec_pre, rec_post);
+                           rec_pp);
         *launches += 1;
         return e;
     }
@@ -176,10 +186,10 @@ cudaError_t launch_fwht_log_table(int r, const FieldTables &t, uint32_t lgn, uin
 
 cudaError_t launch_locator(int r, const FieldTables &t, uint32_t lgn, const MaskBits &bits, const uint32_t *fl,
                            uint32_t *work, uint16_t *pre, uint16_t *post, cudaStream_t s, uint64_t *launches,
-                           uint8_t *rec_pre, uint8_t *rec_post)
+                           uint8_t *rec_pp)
 {
-    if (r == 8) return run<8>(1, t, lgn, &bits, fl, nullptr, work, pre, post, s, launches, rec_pre, rec_post);
-    return run<16>(1, t, lgn, &bits, fl, nullptr, work, pre, post, s, launches, rec_pre, rec_post);
+    if (r == 8) return run<8>(1, t, lgn, &bits, fl, nullptr, work, pre, post, s, launches, rec_pp);
+    return run<16>(1, t, lgn, &bits, fl, nullptr, work, pre, post, s, launches, rec_pp);
 }
 
 } // namespace lch

@@ -1092,8 +1092,15 @@ __global__ void __launch_bounds__(kThreads)
 //   the formal derivative: u = B . phi, the neighbour sums of Sec. IV, B^-1;
 //   Psi_n^0 of the result; and F(j) = hatF'(j) / Pi'(j) on the erased rows.
 // Shared memory: the factor records of Psi_n^0 (n - 1, kept for both
-// transforms), one per-row record set (Pi, B, B^-1 and 1/Pi' in turn), the
-// data tile and the derivative's accumulator tile, each n rows x 2^lg_cw bytes.
+// transforms), one per-row record set (Pi | 1/Pi', B and B^-1 in turn: a
+// surviving row takes Pi, an erased one 1/Pi', so one set serves the first
+// and the last step), the data tile and the derivative's accumulator tile,
+// each n rows x 2^lg_cw bytes.  The kernel is persistent: a CTA stages the
+// factor records once and walks column slices, and the next slice's rows
+// are copied in, with the Pi | 1/Pi' records, while the current slice's
+// forward transform runs.  Slices are 2^lg_cw bytes wide for `full` rounds
+// of the grid; the columns left after them go as half-width slices, so that
+// the last round is not a few CTAs working while the others idle.
 struct FusedDecArgs {
     uint8_t *shards;
     size_t S;
@@ -1101,7 +1108,7 @@ struct FusedDecArgs {
     const uint8_t *rec;             // factor records of every level
     const uint8_t *brec, *binvrec;  // records of B_j and B_j^-1
     const uint16_t *pre, *post;     // Pi(j) off E (0 on E); 1/Pi'(j) on E (0 off E)
-    const uint8_t *prerec, *postrec; // their records (n, region layout), or null: built here
+    const uint8_t *pprec;           // records of pre | post (n, region layout), or null: built here
 };
 
 template <int R>
@@ -1111,11 +1118,15 @@ __host__ __device__ __forceinline__ size_t fused_dec_smem(uint32_t lgn, uint32_t
     return (size_t)tab_bytes<R>(n - 1) + tab_bytes<R>(n) + (2ull * n << lg_cw);
 }
 
-// x_row <- c_row x_row for every word of the tile, c_row's record at row in srec.
+// x_row <- c_row x_row for every word of the tile, c_row's record at row in
+// srec; with `nz`, only the rows whose nz entry is not zero (the others hold
+// zeros and keep them).
 template <int R>
-__device__ __forceinline__ void tile_rows_mul(uint32_t sdata, uint32_t srec, uint32_t n, uint32_t lg_w)
+__device__ __forceinline__ void tile_rows_mul(uint32_t sdata, uint32_t srec, uint32_t n, uint32_t lg_w,
+                                              const uint16_t *nz = nullptr)
 {
     for (uint32_t it = threadIdx.x; it < (n << lg_w); it += blockDim.x) {
+        if (nz && nz[it >> lg_w] == 0) continue;
         const uint32_t p = sdata + (it << 2);
         sts_u32(p, MulK<R, 0>::f(lds_u32(p), tab_ref<R>(srec, it >> lg_w, n)));
     }
@@ -1169,24 +1180,65 @@ __device__ __forceinline__ void tile_nbr_sums(uint32_t su, uint32_t sacc, uint32
 #undef LCH_NS
 }
 
+// Work item y of the slicing described above: its first column and log2 width.
+struct DecSlice {
+    size_t col;
+    uint32_t lgc;
+};
+__device__ __forceinline__ DecSlice dec_slice(uint32_t y, uint32_t lg_cw, uint32_t nfull)
+{
+    if (y < nfull) return {(size_t)y << lg_cw, lg_cw};
+    return {((size_t)nfull << lg_cw) + ((size_t)(y - nfull) << (lg_cw - 1)), lg_cw - 1};
+}
+
 // NT threads: 1024 when a slice has at least 4096 words (32 warps hide the
 // barriers between the decode's many short phases better: medium_gf16 96 us
 // against 102 at 512), else 512.
 template <int R, int NT>
-__global__ void __launch_bounds__(NT, 1) k_fused_dec(FusedDecArgs a, uint32_t lg_cw)
+__global__ void __launch_bounds__(NT, 1) k_fused_dec(FusedDecArgs a, uint32_t lg_cw, uint32_t nfull, uint32_t nitems)
 {
     extern __shared__ __align__(128) uint8_t sm[];
     constexpr uint32_t cpr = FT<R>::rec_bytes / 16;
     const uint32_t lgn = a.lgn, n = 1u << lgn;
-    const uint32_t lg_w = lg_cw - 2, lg_vpr = lg_cw - 4, cw = 1u << lg_cw;
     uint8_t *rrec = sm + tab_bytes<R>(n - 1);
     uint8_t *t0 = rrec + tab_bytes<R>(n);
     uint8_t *t1 = t0 + (n << lg_cw);
     const uint32_t sf = (uint32_t)__cvta_generic_to_shared(sm), sr = (uint32_t)__cvta_generic_to_shared(rrec);
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(t0), s1 = (uint32_t)__cvta_generic_to_shared(t1);
-    const size_t col = (size_t)blockIdx.x << lg_cw;
-    const size_t rem = a.S - col;
-    const uint32_t width = rem < cw ? (uint32_t)rem : cw;
+    auto slice_width = [&](const DecSlice &d) {
+        const size_t rem = a.S > d.col ? a.S - d.col : 0;
+        return rem < (1u << d.lgc) ? (uint32_t)rem : (1u << d.lgc);
+    };
+    // Phi = F . Pi starts from the surviving rows of the slice; erased rows
+    // (and the ragged tail) are zero
+    auto issue_rows = [&](const DecSlice &d) {
+        const size_t col = d.col;
+        const uint32_t width = slice_width(d), lg_vpr = d.lgc - 4;
+        for (uint32_t v = threadIdx.x; v < (n << lg_vpr); v += blockDim.x) {
+            const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
+            if (a.pre[m] != 0 && c * 16 < width)
+                cp_async16(t0 + v * 16, a.shards + (size_t)m * a.S + col + c * 16);
+            else
+                *reinterpret_cast<uint4 *>(t0 + v * 16) = make_uint4(0, 0, 0, 0);
+        }
+    };
+    auto stage_rows_recs = [&](const uint8_t *src) {
+        for (uint32_t v = threadIdx.x; v < n * cpr; v += blockDim.x) {
+            const uint32_t q = v / cpr, c = v - q * cpr;
+            cp_async16(rrec + rec_dst<R>(n, q, c), src + (size_t)q * FT<R>::rec_bytes + c * 16);
+        }
+    };
+    auto stage_pp = [&]() {
+        if (a.pprec) {
+            for (uint32_t v = threadIdx.x; v < tab_bytes<R>(n) / 16; v += blockDim.x)
+                cp_async16(rrec + v * 16, a.pprec + v * 16);
+        } else {
+            for (uint32_t v = threadIdx.x; v < n * cpr; v += blockDim.x) {
+                const uint32_t q = v / cpr, c = v - q * cpr;
+                *reinterpret_cast<uint4 *>(rrec + rec_dst<R>(n, q, c)) = rec_chunk<R>(a.pre[q] | a.post[q], c);
+            }
+        }
+    };
 
     pdl_trigger();
     {
@@ -1196,71 +1248,61 @@ __global__ void __launch_bounds__(NT, 1) k_fused_dec(FusedDecArgs a, uint32_t lg
         p.l = 0;
         stage_pass_recs<R>(p, n, 0, sm); // static tables
     }
-    pdl_wait(); // pre/post and the shards come from predecessors
+    pdl_wait(); // pre/post, their records and the shards come from predecessors
+    // items past the last column (a ragged S leaves some half slices empty)
+    // are skipped by the whole CTA
+    auto next_item = [&](uint32_t y) {
+        while (y < nitems && dec_slice(y, lg_cw, nfull).col >= a.S) y += gridDim.x;
+        return y;
+    };
+    uint32_t y = next_item(blockIdx.x);
+    if (y < nitems) issue_rows(dec_slice(y, lg_cw, nfull));
+    stage_pp();
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
 
-    // Phi = F . Pi: survivors in, erased rows (and the ragged tail) zero
-    for (uint32_t v = threadIdx.x; v < (n << lg_vpr); v += blockDim.x) {
-        const uint32_t m = v >> lg_vpr, c = v & ((1u << lg_vpr) - 1u);
-        if (a.pre[m] != 0 && c * 16 < width)
-            cp_async16(t0 + v * 16, a.shards + (size_t)m * a.S + col + c * 16);
-        else
-            *reinterpret_cast<uint4 *>(t0 + v * 16) = make_uint4(0, 0, 0, 0);
-    }
-    if (a.prerec) {
-        for (uint32_t v = threadIdx.x; v < tab_bytes<R>(n) / 16; v += blockDim.x)
-            cp_async16(rrec + v * 16, a.prerec + v * 16);
-    } else {
-        for (uint32_t v = threadIdx.x; v < n * cpr; v += blockDim.x) {
-            const uint32_t q = v / cpr, c = v - q * cpr;
-            *reinterpret_cast<uint4 *>(rrec + rec_dst<R>(n, q, c)) = rec_chunk<R>(a.pre[q], c);
-        }
-    }
-    cp_async_commit();
-    cp_async_wait_all();
-    __syncthreads();
-    tile_rows_mul<R>(s0, sr, n, lg_w);
-    __syncthreads();
-    // the records of B, copied in while the inverse transform runs
-    for (uint32_t v = threadIdx.x; v < n * cpr; v += blockDim.x) {
-        const uint32_t q = v / cpr, c = v - q * cpr;
-        cp_async16(rrec + rec_dst<R>(n, q, c), a.brec + (size_t)q * FT<R>::rec_bytes + c * 16);
-    }
-    cp_async_commit();
-    tile_levels<R, 1>(s0, sf, lgn, lg_w); // Algorithm 2: coefficients of hatF
-    cp_async_wait_all();
-    __syncthreads();
-    tile_rows_mul<R>(s0, sr, n, lg_w); // u = B . phi
-    __syncthreads();
-    for (uint32_t v = threadIdx.x; v < n * cpr; v += blockDim.x) {
-        const uint32_t q = v / cpr, c = v - q * cpr;
-        cp_async16(rrec + rec_dst<R>(n, q, c), a.binvrec + (size_t)q * FT<R>::rec_bytes + c * 16);
-    }
-    cp_async_commit();
-    tile_nbr_sums<R>(s0, s1, lgn, lg_w);
-    cp_async_wait_all();
-    __syncthreads();
-    tile_rows_mul<R>(s1, sr, n, lg_w); // the derivative's coefficients, B^-1 (sums)
-    __syncthreads();
-    if (a.postrec) {
-        for (uint32_t v = threadIdx.x; v < tab_bytes<R>(n) / 16; v += blockDim.x)
-            cp_async16(rrec + v * 16, a.postrec + v * 16);
+    while (y < nitems) {
+        const DecSlice d = dec_slice(y, lg_cw, nfull);
+        const size_t col = d.col;
+        const uint32_t width = slice_width(d), lg_w = d.lgc - 2;
+        const uint32_t ynext = next_item(y + gridDim.x);
+        tile_rows_mul<R>(s0, sr, n, lg_w, a.pre); // Phi = F . Pi (the erased rows stay zero)
+        __syncthreads();
+        stage_rows_recs(a.brec); // the records of B, copied in while the inverse transform runs
         cp_async_commit();
-    } else {
-        for (uint32_t v = threadIdx.x; v < n * cpr; v += blockDim.x) {
-            const uint32_t q = v / cpr, c = v - q * cpr;
-            *reinterpret_cast<uint4 *>(rrec + rec_dst<R>(n, q, c)) = rec_chunk<R>(a.post[q], c);
+        tile_levels<R, 1>(s0, sf, lgn, lg_w); // Algorithm 2: coefficients of hatF
+        cp_async_wait_all();
+        __syncthreads();
+        tile_rows_mul<R>(s0, sr, n, lg_w); // u = B . phi
+        __syncthreads();
+        stage_rows_recs(a.binvrec);
+        cp_async_commit();
+        tile_nbr_sums<R>(s0, s1, lgn, lg_w);
+        cp_async_wait_all();
+        __syncthreads();
+        tile_rows_mul<R>(s1, sr, n, lg_w); // the derivative's coefficients, B^-1 (sums)
+        __syncthreads();
+        // while the forward transform runs on t1: the records of Pi | 1/Pi'
+        // (this slice's last step and the next slice's first) and the next
+        // slice's rows into t0, which the derivative no longer needs
+        stage_pp();
+        if (ynext < nitems) issue_rows(dec_slice(ynext, lg_cw, nfull));
+        cp_async_commit();
+        tile_levels<R, 0>(s1, sf, lgn, lg_w); // hatF' at every point
+        cp_async_wait_all();
+        __syncthreads();
+        // F(j) = hatF'(j) / Pi'(j), written to the erased rows only.  No
+        // barrier after it: the next slice's first step works on t0 and, like
+        // this one, only reads the records.
+        for (uint32_t it = threadIdx.x; it < (n << lg_w); it += blockDim.x) {
+            const uint32_t row = it >> lg_w, w = it & ((1u << lg_w) - 1u);
+            if (a.post[row] != 0 && w * 4 < width) {
+                const uint32_t x = MulK<R, 0>::f(lds_u32(s1 + (it << 2)), tab_ref<R>(sr, row, n));
+                *reinterpret_cast<uint32_t *>(a.shards + (size_t)row * a.S + col + w * 4) = x;
+            }
         }
-    }
-    tile_levels<R, 0>(s1, sf, lgn, lg_w); // hatF' at every point
-    cp_async_wait_all();
-    __syncthreads();
-    // F(j) = hatF'(j) / Pi'(j), written to the erased rows only
-    for (uint32_t it = threadIdx.x; it < (n << lg_w); it += blockDim.x) {
-        const uint32_t row = it >> lg_w, w = it & ((1u << lg_w) - 1u);
-        if (a.post[row] != 0 && w * 4 < width) {
-            const uint32_t x = MulK<R, 0>::f(lds_u32(s1 + (it << 2)), tab_ref<R>(sr, row, n));
-            *reinterpret_cast<uint32_t *>(a.shards + (size_t)row * a.S + col + w * 4) = x;
-        }
+        y = ynext;
     }
 }
 
@@ -1885,21 +1927,32 @@ uint32_t fused_dec_lg_cw(int r, uint32_t lgn, size_t S)
 }
 
 cudaError_t launch_fused_decode(int r, const FieldTables &t, uint32_t lgn, uint8_t *shards, size_t S,
-                                const uint16_t *pre, const uint16_t *post, const uint8_t *prerec,
-                                const uint8_t *postrec, uint32_t lg_cw, cudaStream_t s, uint64_t *launches)
+                                const uint16_t *pre, const uint16_t *post, const uint8_t *pprec, uint32_t lg_cw,
+                                cudaStream_t s, uint64_t *launches)
 {
-    const FusedDecArgs a{shards, S, lgn, t.rec, t.brec, t.binvrec, pre, post, prerec, postrec};
-    const dim3 grid((unsigned)((S + (1ull << lg_cw) - 1) >> lg_cw));
+    const FusedDecArgs a{shards, S, lgn, t.rec, t.brec, t.binvrec, pre, post, pprec};
+    const uint32_t nslices = (uint32_t)((S + (1ull << lg_cw) - 1) >> lg_cw);
+    // persistent: at most one CTA per SM (the shared memory allows no more).
+    // Full-width slices for whole rounds of the grid; what is left after
+    // them goes as half-width slices when those fit one round.
+    const uint32_t G = std::min<uint32_t>(nslices, (uint32_t)device_sms());
+    const uint32_t rest = nslices % G;
+    uint32_t nfull = nslices, nitems = nslices;
+    if (rest != 0 && nslices > G && lg_cw > 4 && 2 * rest <= G) {
+        nfull = nslices - rest;
+        nitems = nfull + 2 * rest;
+    }
+    const dim3 grid(G);
     cudaError_t e;
     {
         const bool wide = ((1u << lgn) << (lg_cw - 2)) >= 4096;
         const size_t smem = r == 8 ? fused_dec_smem<8>(lgn, lg_cw) : fused_dec_smem<16>(lgn, lg_cw);
         if (r == 8)
-            e = wide ? launch_pdl(k_fused_dec<8, 1024>, grid, dim3(1024), smem, s, a, lg_cw)
-                     : launch_pdl(k_fused_dec<8, 512>, grid, dim3(512), smem, s, a, lg_cw);
+            e = wide ? launch_pdl(k_fused_dec<8, 1024>, grid, dim3(1024), smem, s, a, lg_cw, nfull, nitems)
+                     : launch_pdl(k_fused_dec<8, 512>, grid, dim3(512), smem, s, a, lg_cw, nfull, nitems);
         else
-            e = wide ? launch_pdl(k_fused_dec<16, 1024>, grid, dim3(1024), smem, s, a, lg_cw)
-                     : launch_pdl(k_fused_dec<16, 512>, grid, dim3(512), smem, s, a, lg_cw);
+            e = wide ? launch_pdl(k_fused_dec<16, 1024>, grid, dim3(1024), smem, s, a, lg_cw, nfull, nitems)
+                     : launch_pdl(k_fused_dec<16, 512>, grid, dim3(512), smem, s, a, lg_cw, nfull, nitems);
     }
     *launches += 1;
     return e;

@@ -605,7 +605,7 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
     const uint32_t fused_lg_cw = packed ? 0 : fused_dec_lg_cw(field, lgn, S);
     const size_t rec_set = field == LCH_GF16 ? tab_bytes<16>(n) : tab_bytes<8>(n);
     const size_t off_rec = off_list + align_up(sizeof(uint32_t) * n);
-    rc = ensure_scratch(ctx, off_rec + (fused_lg_cw ? 2 * align_up(rec_set) : 0));
+    rc = ensure_scratch(ctx, off_rec + (fused_lg_cw ? align_up(rec_set) : 0));
     if (rc) return rc;
     uint8_t *phi = ctx->scratch, *phi2 = ctx->scratch + off_phi2;
     const uint16_t *pre = reinterpret_cast<uint16_t *>(ctx->scratch + off_pre);
@@ -621,22 +621,20 @@ int decode_impl(lch_ctx *ctx, uint32_t n, uint32_t k, int field, uint8_t *shards
         if (rc) return rc;
         const FieldTables &t = ctx->tab[field == LCH_GF16];
         // Step 1: Pi(j) off E and 1/Pi'(j) on E.
-        // (with the records of Pi and 1/Pi' for the fused decode)
+        // (with the records of Pi and 1/Pi', one set, for the fused decode)
         PROF(LCH_KIND_LOCATOR, 0,
              launch_locator(field, t, lgn, bits, ctx->fl[field == LCH_GF16][lgn], work, wpre, wpost, s, &ctx->launches,
-                            fused_lg_cw ? ctx->scratch + off_rec : nullptr,
-                            fused_lg_cw ? ctx->scratch + off_rec + align_up(rec_set) : nullptr));
+                            fused_lg_cw ? ctx->scratch + off_rec : nullptr));
     }
     const uint64_t cols = S / (field / 8);
     if (fused_lg_cw) {
         // Steps 2-6 in one launch: every transform fits one tile.  With a
         // cached locator each CTA builds the records of Pi and 1/Pi' itself.
         const uint64_t m0 = (uint64_t)n / 2 * lgn - (n - 1);
-        const uint8_t *prerec = loc ? nullptr : ctx->scratch + off_rec;
-        const uint8_t *postrec = loc ? nullptr : ctx->scratch + off_rec + align_up(rec_set);
+        const uint8_t *pprec = loc ? nullptr : ctx->scratch + off_rec;
         PROFM(LCH_KIND_PASS, (uint64_t)n * S, (uint64_t)(n - ne + 2 * m0 + 2 * n + ne) * cols,
-              launch_fused_decode(field, ctx->tab[field == LCH_GF16], lgn, shards, S, pre, post, prerec, postrec,
-                                  fused_lg_cw, s, &ctx->launches));
+              launch_fused_decode(field, ctx->tab[field == LCH_GF16], lgn, shards, S, pre, post, pprec, fused_lg_cw, s,
+                                  &ctx->launches));
         return LCH_OK;
     }
     // the erased rows' ranks and list (row addressing of steps 2 and 6)

@@ -308,9 +308,9 @@ cudaError_t launch_deriv(int r, int mode, const DerivArgs &a, cudaStream_t s, ui
 // The decode of Algorithm 2 after the locator, as one launch, for lg n <= 8:
 // fused_dec_lg_cw gives its column-slice width (log2 bytes), 0 when the
 // codeword does not fit the fused form.  pre = Pi off E (0 on E), post =
-// 1/Pi' on E (0 off E); prerec / postrec, when not null, are their records
-// from launch_locator (else each CTA builds them).  Only the erased rows of
-// shards are written.
+// 1/Pi' on E (0 off E); pprec, when not null, is the one record set of
+// pre | post from launch_locator (else each CTA builds it).  Only the erased
+// rows of shards are written.
 uint32_t fused_dec_lg_cw(int r, uint32_t lgn, size_t S);
 // Algorithm 1 as one launch for lg k <= 8 (k a power of two, ncos = n/k - 1
 // cosets written after the message rows); fused_enc_lg_cw as above.
@@ -318,8 +318,8 @@ uint32_t fused_enc_lg_cw(int r, uint32_t lgk, size_t S);
 cudaError_t launch_fused_encode(int r, const FieldTables &t, uint32_t lgk, uint32_t ncos, uint8_t *shards, size_t S,
                                 uint32_t lg_cw, cudaStream_t s, uint64_t *launches);
 cudaError_t launch_fused_decode(int r, const FieldTables &t, uint32_t lgn, uint8_t *shards, size_t S,
-                                const uint16_t *pre, const uint16_t *post, const uint8_t *prerec,
-                                const uint8_t *postrec, uint32_t lg_cw, cudaStream_t s, uint64_t *launches);
+                                const uint16_t *pre, const uint16_t *post, const uint8_t *pprec, uint32_t lg_cw,
+                                cudaStream_t s, uint64_t *launches);
 
 // c = c (.) t elementwise over `bytes` bytes (Sec. VI.A pointwise product).
 cudaError_t launch_pointwise(int r, uint8_t *c, const uint8_t *t, size_t bytes, const FieldTables &tab,
@@ -401,12 +401,12 @@ cudaError_t launch_rank(const MaskBits &bits, uint32_t n, uint32_t *out_bits, ui
 
 cudaError_t launch_fwht_log_table(int r, const FieldTables &t, uint32_t lgn, uint32_t *fl,
                                   uint32_t *work, cudaStream_t s, uint64_t *launches);
-// rec_pre / rec_post (n <= 4096 only; may be null): also the split-table
-// records of pre and post, in the region layout of n records.
+// rec_pp (n <= 4096 only; may be null): also one set of split-table records
+// in the region layout of n records, row j's being that of pre[j] | post[j]
+// (one of the two is zero).
 cudaError_t launch_locator(int r, const FieldTables &t, uint32_t lgn, const MaskBits &bits,
                            const uint32_t *fl, uint32_t *work, uint16_t *pre, uint16_t *post,
-                           cudaStream_t s, uint64_t *launches, uint8_t *rec_pre = nullptr,
-                           uint8_t *rec_post = nullptr);
+                           cudaStream_t s, uint64_t *launches, uint8_t *rec_pp = nullptr);
 
 // ---------------------------------------------------------------- batches
 // One persistent launch runs many codewords: tasks are pulled from a queue in

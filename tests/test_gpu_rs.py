@@ -136,6 +136,41 @@ def test_medium_gf16_workload(ctx):
     assert np.array_equal(gpu_decode(ctx, w.field, w.n, w.k, cw, mask), cw)
 
 
+@pytest.mark.parametrize("r,n,k,S", [(16, 256, 128, 65424), (16, 256, 128, 65488), (8, 256, 64, 40000),
+                                     (16, 128, 64, 175728)])
+def test_fused_decode_slicing_tail(ctx, r, n, k, S):
+    """The fused short-codeword decode is persistent over column slices; the
+    columns left after whole rounds of the grid go as half-width slices, the
+    last of them partial or (when S ends early in its slice) empty.  Every
+    erased row against the codeword, sampled columns against the oracle."""
+    host = message(n, k, S, seed=S + n)
+    cw = gpu_encode(ctx, r, n, k, host)
+    mask = WL.erasure_mask(n, n - k, seed=S)
+    got = gpu_decode(ctx, r, n, k, cw, mask)
+    assert np.array_equal(got, cw)
+    cols = elem_cols(S, r, 6, seed=1)
+    bad = elems(cw, r, cols)
+    bad[mask == 1] = 0
+    rows = np.nonzero(mask)[0][:64]
+    ref = O.rs_decode(r, n, k, bad, mask, rows=rows)
+    assert np.array_equal(elems(got, r, cols)[rows], ref[rows])
+
+
+def test_fused_decode_cached_locator_wide_shards():
+    """A shortened code (k not a power of two) encodes by a decode with the
+    cached locator, whose records each CTA of the fused decode builds for
+    every slice it walks; wide shards take the half-width tail as well."""
+    ctx2 = lch.Context(0)
+    try:
+        r, n, k, S = 16, 256, 200, 65424
+        host = message(n, k, S, seed=4242)
+        got = gpu_encode(ctx2, r, n, k, host)
+        cols = elem_cols(S, r, 6, seed=3)
+        assert np.array_equal(elems(got, r)[:, cols], O.rs_encode(r, n, k, elems(host, r, cols)))
+    finally:
+        ctx2.close()
+
+
 def test_large_gf16_workload(ctx):
     """n = 65536, k = 32768, 4 KiB shards: all 32768 parity rows of 4 element
     columns (the first, the last and two seeded ones) against the oracle's
