@@ -9,7 +9,8 @@
 // exponent then gives Pi(j) for surviving j and Pi'(j) for erased j, the
 // denominators of Algorithm 2 step 6 (eqs. Pi(j), Pi'(j)).
 //
-// n <= 2^12 runs in one CTA in shared memory.  Larger n splits the index bits
+// n <= 2^12 runs in one CTA in shared memory (several when the fused decode
+// wants the records of Pi and 1/Pi' as well).  Larger n splits the index bits
 // into a low group (contiguous tiles) and a high group (strided tiles): the
 // two groups' Hadamard factors commute, so FWHT = FWHT_low o FWHT_high and the
 // pointwise product sits between the two high-group halves:
@@ -17,19 +18,32 @@
 //   pass B: FWHT_high, * FWHT(L), FWHT_high  (strided tiles)
 //   pass C: FWHT_low, scale, exponent        (contiguous tiles)
 // FWHT(L) itself is passes A and B on L.
+#include <cstring>
+
 #include "lch_internal.cuh"
 
 namespace lch {
 
 namespace {
 
+constexpr uint32_t kSmallLg = 12;
+
+// The erasure bitmap of a codeword of at most 2^kSmallLg rows, passed by
+// value: 512 bytes of kernel parameters instead of the 8 KB of a full one.
+struct SmallMask {
+    uint32_t w[(1u << kSmallLg) / 32];
+};
+__device__ __forceinline__ uint32_t mask_bit(const SmallMask &b, uint32_t j) { return (b.w[j >> 5] >> (j & 31u)) & 1u; }
+
 // MODE 0: FWHT(L) -> fl_out.  MODE 1: full locator -> pre/post.
 // MODE 1 with rec_pp: also one set of split-table records, in the region
 // layout of n records, for the fused short-codeword decode: row j's record is
 // that of Pi(j) when j survives and of 1/Pi'(j) when j is erased (every row
-// needs exactly one of the two).
+// needs exactly one of the two).  Building the records is most of the work,
+// so that form runs on several CTAs: each one computes the (short) FWHTs and
+// builds its share of the record chunks; CTA 0 writes pre and post.
 template <int R, int MODE>
-__global__ void __launch_bounds__(1024) k_loc_small(uint32_t lgn, MaskBits bits, const uint16_t *__restrict__ logt,
+__global__ void __launch_bounds__(1024) k_loc_small(uint32_t lgn, SmallMask bits, const uint16_t *__restrict__ logt,
                                                     const uint16_t *__restrict__ expt, const uint32_t *__restrict__ fl,
                                                     uint32_t *fl_out, uint16_t *pre, uint16_t *post, uint32_t ninv,
                                                     uint8_t *rec_pp)
@@ -55,12 +69,14 @@ __global__ void __launch_bounds__(1024) k_loc_small(uint32_t lgn, MaskBits bits,
                 const uint32_t cj = mmul<R>(v[j], ninv);
                 const bool e = mask_bit(bits, j);
                 const uint32_t kp = e ? 0u : expt[cj], kd = e ? expt[cj == 0 ? 0 : M - cj] : 0u;
-                pre[j] = (uint16_t)kp;
-                post[j] = (uint16_t)kd;
+                if (blockIdx.x == 0) {
+                    pre[j] = (uint16_t)kp;
+                    post[j] = (uint16_t)kd;
+                }
                 v[j] = kp | kd;
             }
             __syncthreads();
-            for (uint32_t i = threadIdx.x; i < n * cpr; i += blockDim.x) {
+            for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n * cpr; i += gridDim.x * blockDim.x) {
                 const uint32_t q = i / cpr, c = i - q * cpr;
                 *reinterpret_cast<uint4 *>(rec_pp + rec_dst<R>(n, q, c)) = rec_chunk<R>(v[q], c);
             }
@@ -130,8 +146,6 @@ __global__ void __launch_bounds__(256) k_loc_c(uint32_t a, MaskBits bits, const 
     }
 }
 
-constexpr uint32_t kSmallLg = 12;
-
 template <int R>
 cudaError_t run(int mode, const FieldTables &t, uint32_t lgn, const MaskBits *bits, const uint32_t *fl,
                 uint32_t *fl_out, uint32_t *work, uint16_t *pre, uint16_t *post, cudaStream_t s, uint64_t *launches,
@@ -144,14 +158,17 @@ cudaError_t run(int mode, const FieldTables &t, uint32_t lgn, const MaskBits *bi
     cudaError_t e;
     if (lgn <= kSmallLg) {
         const uint32_t n = 1u << lgn;
-        // the record chunks (n x rec_bytes / 16 of them) want every thread
+        SmallMask smask;
+        memcpy(smask.w, mb.w, sizeof(smask.w));
+        // the record chunks (n x rec_bytes / 16 of them): one per thread
         const unsigned threads = rec_pp ? 1024 : n < 1024 ? (n < 32 ? 32 : n) : 1024;
+        const unsigned ctas = rec_pp ? (n * (FT<R>::rec_bytes / 16) + 1023) / 1024 : 1;
         const size_t smem = sizeof(uint32_t) * n;
         if (mode == 0)
-            e = launch_pdl(k_loc_small<R, 0>, dim3(1), dim3(threads), smem, s, lgn, mb, t.logt, t.expt, fl, fl_out, pre, post, ninv,
+            e = launch_pdl(k_loc_small<R, 0>, dim3(1), dim3(threads), smem, s, lgn, smask, t.logt, t.expt, fl, fl_out, pre, post, ninv,
                            (uint8_t *)nullptr);
         else
-            e = launch_pdl(k_loc_small<R, 1>, dim3(1), dim3(threads), smem, s, lgn, mb, t.logt, t.expt, fl, fl_out, pre, post, ninv,
+            e = launch_pdl(k_loc_small<R, 1>, dim3(ctas), dim3(threads), smem, s, lgn, smask, t.logt, t.expt, fl, fl_out, pre, post, ninv,
                            rec_pp);
         *launches += 1;
         return e;

@@ -91,6 +91,7 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t a)
     return v;
 }
 __device__ __forceinline__ void sts_u32(uint32_t a, uint32_t v) { asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v)); }
+__device__ __forceinline__ void sts_u16(uint32_t a, uint32_t v) { asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "r"(v)); }
 
 // c * w for the two GF(2^16) elements packed in w; the table bases in t are
 // shared-window addresses, OFF0/OFF2 compile-time record offsets.
@@ -1159,6 +1160,113 @@ __device__ __forceinline__ void tile_levels(uint32_t sdata, uint32_t stab, uint3
     }
 }
 
+// GF(2^16) rounds with one element per thread ("element lanes"): the
+// 256-row tiles of the fused decode give the word rounds (two elements per
+// thread) only (n / 16) x words work items, half the threads of its CTA;
+// element lanes give every thread one.  Same butterflies, one element's
+// three lookups per product.
+template <uint32_t OFF0, uint32_t OFF2>
+__device__ __forceinline__ uint32_t mul16e(uint32_t x, const TabRef<16> &t)
+{
+    return lds_u16<OFF0>(((x << 1) & 0x7Eu) | t.b0) ^ lds_u16<OFF0>(((x >> 5) & 0x7Eu) | t.b1) ^
+           lds_u16<OFF2>(((x >> 11) & 0x1Eu) | t.b2);
+}
+
+template <int INV, int Q, int J, int U, bool ZT>
+struct ELevelStep {
+    static __device__ __forceinline__ void run(uint32_t *x, const TabRef<16> &t)
+    {
+        if constexpr (U < (1 << Q)) {
+            if constexpr ((U & (1 << J)) == 0) {
+                constexpr uint32_t K = (uint32_t)(U >> (J + 1));
+                uint32_t &A = x[U];
+                uint32_t &B = x[U | (1 << J)];
+                if constexpr (ZT && U < (1 << J)) {
+                    B ^= A;
+                } else if constexpr (INV) {
+                    B ^= A;
+                    A ^= mul16e<K * 128, K * 32>(B, t);
+                } else {
+                    A ^= mul16e<K * 128, K * 32>(B, t);
+                    B ^= A;
+                }
+            }
+            ELevelStep<INV, Q, J, U + 1, ZT>::run(x, t);
+        }
+    }
+};
+
+template <int INV, int Q, int JJ, bool ZT>
+__device__ __forceinline__ void eround_levels(uint32_t *x, uint32_t tab, uint32_t nrec, uint32_t nrows, uint32_t base,
+                                              uint32_t s0)
+{
+    if constexpr (JJ < Q) {
+        constexpr int J = INV ? JJ : Q - 1 - JJ;
+        const uint32_t s = s0 + J;
+        const TabRef<16> t = tab_ref<16>(tab, rec_base(nrows, s) + (base >> (s + 1)), nrec);
+        ELevelStep<INV, Q, J, 0, ZT>::run(x, t);
+        eround_levels<INV, Q, JJ + 1, ZT>(x, tab, nrec, nrows, base, s0);
+    }
+}
+
+// As round_q (on the tile, the whole CTA), one element column per item.
+template <int INV, int Q, bool ZT>
+__device__ __forceinline__ void eround_q(uint32_t data, uint32_t tab, uint32_t nrec, uint32_t nrows, uint32_t lg_w,
+                                         uint32_t s0)
+{
+    const uint32_t lg_e = lg_w + 1;
+    const uint32_t items = (nrows >> Q) << lg_e;
+    const uint32_t stride = 4u << (s0 + lg_w);
+    for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
+        const uint32_t g = it >> lg_e, e = it & ((1u << lg_e) - 1u);
+        const uint32_t base = ((g >> s0) << (s0 + Q)) | (g & ((1u << s0) - 1u));
+        const uint32_t p = data + (base << (lg_w + 2)) + (e << 1);
+        uint32_t x[1 << Q];
+#pragma unroll
+        for (int u = 0; u < (1 << Q); u++) x[u] = lds_u16<0>(p + u * stride);
+        eround_levels<INV, Q, 0, ZT>(x, tab, nrec, nrows, base, s0);
+#pragma unroll
+        for (int u = 0; u < (1 << Q); u++) sts_u16(p + u * stride, x[u]);
+    }
+}
+
+template <int INV, bool ZT>
+__device__ __forceinline__ void eround(uint32_t q, uint32_t data, uint32_t tab, uint32_t nrec, uint32_t nrows,
+                                       uint32_t lg_w, uint32_t s0)
+{
+    switch (q) {
+    case 1: eround_q<INV, 1, ZT>(data, tab, nrec, nrows, lg_w, s0); break;
+    case 2: eround_q<INV, 2, ZT>(data, tab, nrec, nrows, lg_w, s0); break;
+    case 3: eround_q<INV, 3, ZT>(data, tab, nrec, nrows, lg_w, s0); break;
+    default: eround_q<INV, 4, ZT>(data, tab, nrec, nrows, lg_w, s0); break;
+    }
+}
+
+// tile_levels in element lanes (GF(2^16)).
+template <int INV>
+__device__ __forceinline__ void tile_levels_e(uint32_t sdata, uint32_t stab, uint32_t nlev, uint32_t lg_w)
+{
+    const uint32_t nrows = 1u << nlev, nrec = nrows - 1;
+    const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, qb = nlev - qa;
+    if (INV) {
+        if (qb) {
+            eround<INV, false>(qa, sdata, stab, nrec, nrows, lg_w, 0);
+            __syncthreads();
+            eround<INV, true>(qb, sdata, stab, nrec, nrows, lg_w, qa);
+        } else {
+            eround<INV, true>(qa, sdata, stab, nrec, nrows, lg_w, 0);
+        }
+    } else {
+        if (qb) {
+            eround<INV, true>(qb, sdata, stab, nrec, nrows, lg_w, qa);
+            __syncthreads();
+            eround<INV, false>(qa, sdata, stab, nrec, nrows, lg_w, 0);
+        } else {
+            eround<INV, true>(qa, sdata, stab, nrec, nrows, lg_w, 0);
+        }
+    }
+}
+
 // Neighbour sums of the derivative over all lgn bits: acc_j = XOR of u_{j+2^l}
 // over the bits l clear in j (u in su, the sums in sacc).
 template <int R>
@@ -1271,7 +1379,10 @@ __global__ void __launch_bounds__(NT, 1) k_fused_dec(FusedDecArgs a, uint32_t lg
         __syncthreads();
         stage_rows_recs(a.brec); // the records of B, copied in while the inverse transform runs
         cp_async_commit();
-        tile_levels<R, 1>(s0, sf, lgn, lg_w); // Algorithm 2: coefficients of hatF
+        if constexpr (R == 16) // Algorithm 2: coefficients of hatF
+            tile_levels_e<1>(s0, sf, lgn, lg_w);
+        else
+            tile_levels<R, 1>(s0, sf, lgn, lg_w);
         cp_async_wait_all();
         __syncthreads();
         tile_rows_mul<R>(s0, sr, n, lg_w); // u = B . phi
@@ -1289,7 +1400,10 @@ __global__ void __launch_bounds__(NT, 1) k_fused_dec(FusedDecArgs a, uint32_t lg
         stage_pp();
         if (ynext < nitems) issue_rows(dec_slice(ynext, lg_cw, nfull));
         cp_async_commit();
-        tile_levels<R, 0>(s1, sf, lgn, lg_w); // hatF' at every point
+        if constexpr (R == 16) // hatF' at every point
+            tile_levels_e<0>(s1, sf, lgn, lg_w);
+        else
+            tile_levels<R, 0>(s1, sf, lgn, lg_w);
         cp_async_wait_all();
         __syncthreads();
         // F(j) = hatF'(j) / Pi'(j), written to the erased rows only.  No
