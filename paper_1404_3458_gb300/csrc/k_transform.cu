@@ -1116,7 +1116,8 @@ template <int R>
 __host__ __device__ __forceinline__ size_t fused_dec_smem(uint32_t lgn, uint32_t lg_cw)
 {
     const uint32_t n = 1u << lgn;
-    return (size_t)tab_bytes<R>(n - 1) + tab_bytes<R>(n) + (2ull * n << lg_cw);
+    // + the bitmap of surviving rows (n <= 256 bits)
+    return (size_t)tab_bytes<R>(n - 1) + tab_bytes<R>(n) + (2ull * n << lg_cw) + 32;
 }
 
 // x_row <- c_row x_row for every word of the tile, c_row's record at row in
@@ -1209,10 +1210,29 @@ __device__ __forceinline__ void eround_levels(uint32_t *x, uint32_t tab, uint32_
     }
 }
 
+// The per-row steps a round of the fused decode takes on (ERow):
+//   ER_NONE  none;
+//   ER_PI    before its levels, rows whose bit in `surv` is set are multiplied
+//            by their record in srec (Phi = F . Pi, Algorithm 2 step 2);
+//   ER_OUT   after its levels, rows whose bit is clear are multiplied by their
+//            record in srec and written to global memory (F(j) = hatF'(j) /
+//            Pi'(j), step 6); the other rows are dropped.
+// Only a round whose rows are consecutive (s0 = 0) takes a row step.  The
+// rows of an item are the same for the 32 items of a warp, so the tests of
+// `surv` are uniform branches.
+enum ERow { ER_NONE, ER_PI, ER_OUT };
+struct ERowArgs {
+    uint32_t srec, n;
+    const uint32_t *surv; // bit j: row j survives (shared memory)
+    uint8_t *dst;
+    size_t S, col;
+    uint32_t width;
+};
+
 // As round_q (on the tile, the whole CTA), one element column per item.
-template <int INV, int Q, bool ZT>
+template <int INV, int Q, bool ZT, int ROW>
 __device__ __forceinline__ void eround_q(uint32_t data, uint32_t tab, uint32_t nrec, uint32_t nrows, uint32_t lg_w,
-                                         uint32_t s0)
+                                         uint32_t s0, const ERowArgs &ra)
 {
     const uint32_t lg_e = lg_w + 1;
     const uint32_t items = (nrows >> Q) << lg_e;
@@ -1224,45 +1244,77 @@ __device__ __forceinline__ void eround_q(uint32_t data, uint32_t tab, uint32_t n
         uint32_t x[1 << Q];
 #pragma unroll
         for (int u = 0; u < (1 << Q); u++) x[u] = lds_u16<0>(p + u * stride);
-        eround_levels<INV, Q, 0, ZT>(x, tab, nrec, nrows, base, s0);
+        // with s0 = 0 the item's rows are base .. base + 2^Q - 1, inside one
+        // word of the bitmap (Q <= 4 and base a multiple of 2^Q)
+        const uint32_t sv = ROW != ER_NONE ? ra.surv[base >> 5] >> (base & 31u) : 0u;
+        if constexpr (ROW == ER_PI) {
 #pragma unroll
-        for (int u = 0; u < (1 << Q); u++) sts_u16(p + u * stride, x[u]);
+            for (int u = 0; u < (1 << Q); u++)
+                if ((sv >> u) & 1u) x[u] = mul16e<0, 0>(x[u], tab_ref<16>(ra.srec, base + u, ra.n));
+        }
+        eround_levels<INV, Q, 0, ZT>(x, tab, nrec, nrows, base, s0);
+        if constexpr (ROW == ER_OUT) {
+            if (e * 2 < ra.width) {
+                uint8_t *q = ra.dst + (size_t)base * ra.S + ra.col + e * 2;
+#pragma unroll
+                for (int u = 0; u < (1 << Q); u++)
+                    if (!((sv >> u) & 1u))
+                        *reinterpret_cast<uint16_t *>(q + u * ra.S) =
+                            (uint16_t)mul16e<0, 0>(x[u], tab_ref<16>(ra.srec, base + u, ra.n));
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < (1 << Q); u++) sts_u16(p + u * stride, x[u]);
+        }
     }
 }
 
-template <int INV, bool ZT>
+template <int INV, bool ZT, int ROW = ER_NONE>
 __device__ __forceinline__ void eround(uint32_t q, uint32_t data, uint32_t tab, uint32_t nrec, uint32_t nrows,
-                                       uint32_t lg_w, uint32_t s0)
+                                       uint32_t lg_w, uint32_t s0, const ERowArgs &ra = ERowArgs{})
 {
     switch (q) {
-    case 1: eround_q<INV, 1, ZT>(data, tab, nrec, nrows, lg_w, s0); break;
-    case 2: eround_q<INV, 2, ZT>(data, tab, nrec, nrows, lg_w, s0); break;
-    case 3: eround_q<INV, 3, ZT>(data, tab, nrec, nrows, lg_w, s0); break;
-    default: eround_q<INV, 4, ZT>(data, tab, nrec, nrows, lg_w, s0); break;
+    case 1: eround_q<INV, 1, ZT, ROW>(data, tab, nrec, nrows, lg_w, s0, ra); break;
+    case 2: eround_q<INV, 2, ZT, ROW>(data, tab, nrec, nrows, lg_w, s0, ra); break;
+    case 3: eround_q<INV, 3, ZT, ROW>(data, tab, nrec, nrows, lg_w, s0, ra); break;
+    default: eround_q<INV, 4, ZT, ROW>(data, tab, nrec, nrows, lg_w, s0, ra); break;
     }
 }
 
-// tile_levels in element lanes (GF(2^16)).
-template <int INV>
-__device__ __forceinline__ void tile_levels_e(uint32_t sdata, uint32_t stab, uint32_t nlev, uint32_t lg_w)
+// tile_levels in element lanes (GF(2^16)), with the fused decode's row steps:
+// the inverse transform starts with Phi = F . Pi, the forward transform ends
+// with the division by Pi' and the store of the erased rows.  mid() runs,
+// for the inverse, after the barrier that follows the row step's round (the
+// records of Pi are no longer read past it) and, for the forward transform,
+// before the barrier that precedes its row step's round (where it waits for
+// those records).
+template <int INV, class Mid>
+__device__ __forceinline__ void tile_levels_e(uint32_t sdata, uint32_t stab, uint32_t nlev, uint32_t lg_w,
+                                              const ERowArgs &ra, Mid mid)
 {
     const uint32_t nrows = 1u << nlev, nrec = nrows - 1;
     const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, qb = nlev - qa;
     if (INV) {
         if (qb) {
-            eround<INV, false>(qa, sdata, stab, nrec, nrows, lg_w, 0);
+            eround<INV, false, ER_PI>(qa, sdata, stab, nrec, nrows, lg_w, 0, ra);
             __syncthreads();
+            mid();
             eround<INV, true>(qb, sdata, stab, nrec, nrows, lg_w, qa);
         } else {
-            eround<INV, true>(qa, sdata, stab, nrec, nrows, lg_w, 0);
+            eround<INV, true, ER_PI>(qa, sdata, stab, nrec, nrows, lg_w, 0, ra);
+            __syncthreads();
+            mid();
         }
     } else {
         if (qb) {
             eround<INV, true>(qb, sdata, stab, nrec, nrows, lg_w, qa);
+            mid();
             __syncthreads();
-            eround<INV, false>(qa, sdata, stab, nrec, nrows, lg_w, 0);
+            eround<INV, false, ER_OUT>(qa, sdata, stab, nrec, nrows, lg_w, 0, ra);
         } else {
-            eround<INV, true>(qa, sdata, stab, nrec, nrows, lg_w, 0);
+            mid();
+            __syncthreads();
+            eround<INV, true, ER_OUT>(qa, sdata, stab, nrec, nrows, lg_w, 0, ra);
         }
     }
 }
@@ -1311,6 +1363,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused_dec(FusedDecArgs a, uint32_t lg
     uint8_t *rrec = sm + tab_bytes<R>(n - 1);
     uint8_t *t0 = rrec + tab_bytes<R>(n);
     uint8_t *t1 = t0 + (n << lg_cw);
+    uint32_t *surv = reinterpret_cast<uint32_t *>(t1 + (n << lg_cw));
     const uint32_t sf = (uint32_t)__cvta_generic_to_shared(sm), sr = (uint32_t)__cvta_generic_to_shared(rrec);
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(t0), s1 = (uint32_t)__cvta_generic_to_shared(t1);
     auto slice_width = [&](const DecSlice &d) {
@@ -1367,6 +1420,11 @@ __global__ void __launch_bounds__(NT, 1) k_fused_dec(FusedDecArgs a, uint32_t lg
     if (y < nitems) issue_rows(dec_slice(y, lg_cw, nfull));
     stage_pp();
     cp_async_commit();
+    if (threadIdx.x < 8) {
+        uint32_t b = 0;
+        for (uint32_t j = 0; j < 32 && threadIdx.x * 32 + j < n; j++) b |= (a.pre[threadIdx.x * 32 + j] != 0 ? 1u : 0u) << j;
+        surv[threadIdx.x] = b;
+    }
     cp_async_wait_all();
     __syncthreads();
 
@@ -1375,14 +1433,22 @@ __global__ void __launch_bounds__(NT, 1) k_fused_dec(FusedDecArgs a, uint32_t lg
         const size_t col = d.col;
         const uint32_t width = slice_width(d), lg_w = d.lgc - 2;
         const uint32_t ynext = next_item(y + gridDim.x);
-        tile_rows_mul<R>(s0, sr, n, lg_w, a.pre); // Phi = F . Pi (the erased rows stay zero)
-        __syncthreads();
-        stage_rows_recs(a.brec); // the records of B, copied in while the inverse transform runs
-        cp_async_commit();
-        if constexpr (R == 16) // Algorithm 2: coefficients of hatF
-            tile_levels_e<1>(s0, sf, lgn, lg_w);
-        else
+        const ERowArgs ra{sr, n, surv, a.shards, a.S, col, width};
+        if constexpr (R == 16) {
+            // Phi = F . Pi (the erased rows stay zero), then Algorithm 2: the
+            // coefficients of hatF; the records of B are copied in once the
+            // first round has used those of Pi
+            tile_levels_e<1>(s0, sf, lgn, lg_w, ra, [&] {
+                stage_rows_recs(a.brec);
+                cp_async_commit();
+            });
+        } else {
+            tile_rows_mul<R>(s0, sr, n, lg_w, a.pre); // Phi = F . Pi (the erased rows stay zero)
+            __syncthreads();
+            stage_rows_recs(a.brec); // the records of B, copied in while the inverse transform runs
+            cp_async_commit();
             tile_levels<R, 1>(s0, sf, lgn, lg_w);
+        }
         cp_async_wait_all();
         __syncthreads();
         tile_rows_mul<R>(s0, sr, n, lg_w); // u = B . phi
@@ -1400,20 +1466,26 @@ __global__ void __launch_bounds__(NT, 1) k_fused_dec(FusedDecArgs a, uint32_t lg
         stage_pp();
         if (ynext < nitems) issue_rows(dec_slice(ynext, lg_cw, nfull));
         cp_async_commit();
-        if constexpr (R == 16) // hatF' at every point
-            tile_levels_e<0>(s1, sf, lgn, lg_w);
-        else
-            tile_levels<R, 0>(s1, sf, lgn, lg_w);
-        cp_async_wait_all();
-        __syncthreads();
-        // F(j) = hatF'(j) / Pi'(j), written to the erased rows only.  No
-        // barrier after it: the next slice's first step works on t0 and, like
-        // this one, only reads the records.
-        for (uint32_t it = threadIdx.x; it < (n << lg_w); it += blockDim.x) {
-            const uint32_t row = it >> lg_w, w = it & ((1u << lg_w) - 1u);
-            if (a.post[row] != 0 && w * 4 < width) {
-                const uint32_t x = MulK<R, 0>::f(lds_u32(s1 + (it << 2)), tab_ref<R>(sr, row, n));
-                *reinterpret_cast<uint32_t *>(a.shards + (size_t)row * a.S + col + w * 4) = x;
+        if constexpr (R == 16) {
+            // hatF' at every point, its last round dividing by Pi' and
+            // writing the erased rows (after waiting for the records).  No
+            // barrier after it: the next slice's first round works on t0 and
+            // only reads the records, and the barrier after that round comes
+            // before anything overwrites them.
+            tile_levels_e<0>(s1, sf, lgn, lg_w, ra, [] { cp_async_wait_all(); });
+        } else {
+            tile_levels<R, 0>(s1, sf, lgn, lg_w); // hatF' at every point
+            cp_async_wait_all();
+            __syncthreads();
+            // F(j) = hatF'(j) / Pi'(j), written to the erased rows only.  No
+            // barrier after it: the next slice's first step works on t0 and,
+            // like this one, only reads the records.
+            for (uint32_t it = threadIdx.x; it < (n << lg_w); it += blockDim.x) {
+                const uint32_t row = it >> lg_w, w = it & ((1u << lg_w) - 1u);
+                if (a.post[row] != 0 && w * 4 < width) {
+                    const uint32_t x = MulK<R, 0>::f(lds_u32(s1 + (it << 2)), tab_ref<R>(sr, row, n));
+                    *reinterpret_cast<uint32_t *>(a.shards + (size_t)row * a.S + col + w * 4) = x;
+                }
             }
         }
         y = ynext;
