@@ -41,7 +41,13 @@ __device__ __forceinline__ uint32_t mask_bit(const SmallMask &b, uint32_t j) { r
 // that of Pi(j) when j survives and of 1/Pi'(j) when j is erased (every row
 // needs exactly one of the two).  Building the records is most of the work,
 // so that form runs on several CTAs: each one computes the (short) FWHTs and
-// builds its share of the record chunks; CTA 0 writes pre and post.
+// builds its share of the record chunks (one per thread); CTA 0 writes pre
+// and post.
+// MODE 1 reads only the erasure bitmap (a parameter) and tables that are
+// finished before any call uses them (field tables and FWHT(L), whose builds
+// synchronise), so it computes everything before waiting for its predecessor
+// and only writes after: the computation overlaps the end of the previous
+// kernel, and nothing a predecessor may still read is overwritten early.
 template <int R, int MODE>
 __global__ void __launch_bounds__(1024) k_loc_small(uint32_t lgn, SmallMask bits, const uint16_t *__restrict__ logt,
                                                     const uint16_t *__restrict__ expt, const uint32_t *__restrict__ fl,
@@ -50,7 +56,7 @@ __global__ void __launch_bounds__(1024) k_loc_small(uint32_t lgn, SmallMask bits
 {
     extern __shared__ uint32_t v[];
     pdl_trigger();
-    pdl_wait(); // a predecessor may still read pre/post or the work array
+    if constexpr (MODE == 0) pdl_wait(); // a predecessor may still read the work array
     const uint32_t n = 1u << lgn;
     for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) v[j] = MODE == 0 ? (j ? logt[j] : 0u) : mask_bit(bits, j);
     __syncthreads();
@@ -58,31 +64,34 @@ __global__ void __launch_bounds__(1024) k_loc_small(uint32_t lgn, SmallMask bits
     if constexpr (MODE == 0) {
         for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) fl_out[j] = v[j];
     } else {
+        constexpr uint32_t M = (1u << R) - 1, cpr = FT<R>::rec_bytes / 16;
         for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) v[j] = mmul<R>(v[j], fl[j]);
         __syncthreads();
         fwht_smem<R>(v, lgn);
-        if (rec_pp) {
-            // each row's constant once (its table lookups all in flight
-            // together), kept in v for the record chunks that follow
-            constexpr uint32_t M = (1u << R) - 1, cpr = FT<R>::rec_bytes / 16;
+        // each row's constant (Pi(j) off E, 1/Pi'(j) on E; the other one is
+        // zero), its table lookups all in flight together, kept in v
+        for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
+            const uint32_t cj = mmul<R>(v[j], ninv);
+            const bool e = mask_bit(bits, j);
+            v[j] = e ? expt[cj == 0 ? 0 : M - cj] : expt[cj];
+        }
+        __syncthreads();
+        const uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x;
+        uint4 chunk = make_uint4(0, 0, 0, 0);
+        if (rec_pp && i0 < n * cpr) chunk = rec_chunk<R>(v[i0 / cpr], i0 - i0 / cpr * cpr);
+        pdl_wait(); // from here on the outputs may be overwritten
+        if (blockIdx.x == 0) {
             for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
-                const uint32_t cj = mmul<R>(v[j], ninv);
                 const bool e = mask_bit(bits, j);
-                const uint32_t kp = e ? 0u : expt[cj], kd = e ? expt[cj == 0 ? 0 : M - cj] : 0u;
-                if (blockIdx.x == 0) {
-                    pre[j] = (uint16_t)kp;
-                    post[j] = (uint16_t)kd;
-                }
-                v[j] = kp | kd;
+                pre[j] = (uint16_t)(e ? 0u : v[j]);
+                post[j] = (uint16_t)(e ? v[j] : 0u);
             }
-            __syncthreads();
-            for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n * cpr; i += gridDim.x * blockDim.x) {
+        }
+        if (rec_pp) {
+            for (uint32_t i = i0; i < n * cpr; i += gridDim.x * blockDim.x) {
                 const uint32_t q = i / cpr, c = i - q * cpr;
-                *reinterpret_cast<uint4 *>(rec_pp + rec_dst<R>(n, q, c)) = rec_chunk<R>(v[q], c);
+                *reinterpret_cast<uint4 *>(rec_pp + rec_dst<R>(n, q, c)) = i == i0 ? chunk : rec_chunk<R>(v[q], c);
             }
-        } else {
-            for (uint32_t j = threadIdx.x; j < n; j += blockDim.x)
-                emit<R>(j, mmul<R>(v[j], ninv), mask_bit(bits, j), expt, pre, post);
         }
     }
 }
