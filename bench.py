@@ -23,6 +23,7 @@ codeword); N ranks run N independent replicas and the value is the total.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -575,13 +576,21 @@ def run_serving(ctx, torch, args, rank):
                                payload=pool[:n * S].view(n, S))
                     for i, (r, n, k, S, e) in enumerate(specs[:cnt])]
             torch.cuda.synchronize()
-            if name == "served":
-                srv = SV.Server(ctx, budget, max_inflight=3, max_batch=1024, max_batch_bytes=4 * 10**9)
-                srv.prewarm([(r, n, k, S) for (r, n, k, S, e) in specs])
-                st = srv.run(reqs)
-                del srv
-            else:
-                st = SV.serve_plain(ctx, reqs, budget)
+            # no garbage collection inside a timed run: a full collection
+            # over the objects the earlier sections leave behind pauses the
+            # loop, and at 1 k req/s a single pause sets the p99
+            gc.collect()
+            gc.disable()
+            try:
+                if name == "served":
+                    srv = SV.Server(ctx, budget, max_inflight=3, max_batch=1024, max_batch_bytes=4 * 10**9)
+                    srv.prewarm([(r, n, k, S) for (r, n, k, S, e) in specs])
+                    st = srv.run(reqs)
+                    del srv
+                else:
+                    st = SV.serve_plain(ctx, reqs, budget)
+            finally:
+                gc.enable()
             torch.cuda.synchronize()
             torch.cuda.empty_cache()
             res[name] = {k2: (round(v, 3) if isinstance(v, float) else v) for k2, v in st.items()}
