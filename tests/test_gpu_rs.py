@@ -156,6 +156,35 @@ def test_fused_decode_slicing_tail(ctx, r, n, k, S):
     assert np.array_equal(elems(got, r, cols)[rows], ref[rows])
 
 
+@pytest.mark.parametrize("r,n,k,S", [(16, 16, 8, 528), (16, 32, 16, 1040), (16, 32, 8, 4112), (16, 128, 64, 2064),
+                                     (8, 32, 16, 1040), (8, 128, 32, 4112)])
+@pytest.mark.parametrize("kind", ["one", "most", "burst_head", "burst_tail"])
+def test_fused_decode_patterns(ctx, r, n, k, S, kind):
+    """The fused decode across the sizes where its row steps change form
+    (GF(2^16) with lg n < 5 takes separate row passes, from 5 up they ride in
+    the transform rounds), for one erasure, n - k random ones, and bursts at
+    either end of the codeword; every erased row against the oracle's
+    encoding and sampled columns against the oracle's decode."""
+    host = message(n, k, S, seed=31 * n + k)
+    cw = gpu_encode(ctx, r, n, k, host)
+    if kind == "one":
+        mask = WL.erasure_mask(n, 1, seed=n)
+    elif kind == "most":
+        mask = WL.erasure_mask(n, n - k, seed=n + 1)
+    elif kind == "burst_head":
+        mask = WL.burst_mask(n, n - k, 0)
+    else:
+        mask = WL.burst_mask(n, n - k, k)
+    got = gpu_decode(ctx, r, n, k, cw, mask)
+    assert np.array_equal(got, cw)
+    cols = elem_cols(S, r, 4, seed=k)
+    bad = elems(cw, r, cols)
+    bad[mask == 1] = 0
+    rows = np.nonzero(mask)[0][:32]
+    ref = O.rs_decode(r, n, k, bad, mask, rows=rows)
+    assert np.array_equal(elems(got, r, cols)[rows], ref[rows])
+
+
 def test_fused_decode_cached_locator_wide_shards():
     """A shortened code (k not a power of two) encodes by a decode with the
     cached locator, whose records each CTA of the fused decode builds for
