@@ -1086,8 +1086,8 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ------------------------------------------------ fused decode of short codewords
-// When lg n <= 8 every transform of Algorithm 2 fits one tile, so one CTA per
-// column slice runs the whole decode in shared memory after the locator:
+// When lg n <= 8 every transform of Algorithm 2 fits one tile, so a CTA runs
+// the whole decode of a column slice in shared memory after the locator:
 //   Phi = F . Pi on the surviving rows, 0 on the erased ones (eq. hatF(l));
 //   the coefficients (Psi_n^0)^-1 [Phi];
 //   the formal derivative: u = B . phi, the neighbour sums of Sec. IV, B^-1;
@@ -1096,12 +1096,16 @@ __global__ void __launch_bounds__(kThreads)
 // transforms), one per-row record set (Pi | 1/Pi', B and B^-1 in turn: a
 // surviving row takes Pi, an erased one 1/Pi', so one set serves the first
 // and the last step), the data tile and the derivative's accumulator tile,
-// each n rows x 2^lg_cw bytes.  The kernel is persistent: a CTA stages the
-// factor records once and walks column slices, and the next slice's rows
-// are copied in, with the Pi | 1/Pi' records, while the current slice's
-// forward transform runs.  Slices are 2^lg_cw bytes wide for `full` rounds
-// of the grid; the columns left after them go as half-width slices, so that
-// the last round is not a few CTAs working while the others idle.
+// each n rows x 2^lg_cw bytes, and a bitmap of the surviving rows.  The
+// kernel is persistent: a CTA stages the factor records once and walks column
+// slices, and the next slice's rows are copied in, with the Pi | 1/Pi'
+// records, while the current slice's forward transform runs.  Slices are
+// 2^lg_cw bytes wide for whole rounds of the grid (nfull slices); the columns
+// left after them go as half-width slices, so that the last round is not a
+// few CTAs working while the others idle.  In GF(2^16) with 5 to 8 levels the
+// transforms run in element lanes and take the Pi and 1/Pi' steps inside
+// their first and last rounds (tile_levels_e); otherwise every step is a pass
+// over the tile of its own.
 struct FusedDecArgs {
     uint8_t *shards;
     size_t S;
