@@ -1102,10 +1102,10 @@ __global__ void __launch_bounds__(kThreads)
 // records, while the current slice's forward transform runs.  Slices are
 // 2^lg_cw bytes wide for whole rounds of the grid (nfull slices); the columns
 // left after them go as half-width slices, so that the last round is not a
-// few CTAs working while the others idle.  In GF(2^16) with 5 to 8 levels the
-// transforms run in element lanes and take the Pi and 1/Pi' steps inside
-// their first and last rounds (tile_levels_e); otherwise every step is a pass
-// over the tile of its own.
+// few CTAs working while the others idle.  In GF(2^16) the transforms run in
+// element lanes and take the Pi and 1/Pi' steps inside their first and last
+// rounds (tile_levels_e); in GF(2^8) every step is a pass over the tile of
+// its own.
 struct FusedDecArgs {
     uint8_t *shards;
     size_t S;

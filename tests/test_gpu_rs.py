@@ -160,11 +160,12 @@ def test_fused_decode_slicing_tail(ctx, r, n, k, S):
                                      (8, 32, 16, 1040), (8, 128, 32, 4112)])
 @pytest.mark.parametrize("kind", ["one", "most", "burst_head", "burst_tail"])
 def test_fused_decode_patterns(ctx, r, n, k, S, kind):
-    """The fused decode across the sizes where its row steps change form
-    (GF(2^16) with lg n < 5 takes separate row passes, from 5 up they ride in
-    the transform rounds), for one erasure, n - k random ones, and bursts at
-    either end of the codeword; every erased row against the oracle's
-    encoding and sampled columns against the oracle's decode."""
+    """The fused decode in both of its forms (GF(2^16): element-lane
+    transforms with the Pi and 1/Pi' steps inside their first and last
+    rounds, one round per transform up to 16 rows, two above; GF(2^8): a pass
+    per step), for one erasure, n - k random ones, and bursts at either end
+    of the codeword; every erased row against the oracle's encoding and
+    sampled columns against the oracle's decode."""
     host = message(n, k, S, seed=31 * n + k)
     cw = gpu_encode(ctx, r, n, k, host)
     if kind == "one":
