@@ -333,9 +333,12 @@ def run_ours(args):
                               "kernel_bytes_per_step": int(sum(v["bytes"] for v in kinds.values()) / args.steps),
                               "kernel_bytes_over_alg": round(sum(v["bytes"] for v in kinds.values()) / args.steps
                                                              / alg_bytes, 2),
-                              "full_buffer_kernels": ("encode 3 transform passes; decode 7 (row scaling, 4 "
-                                                      "transform passes, 2 derivative passes) plus the division "
-                                                      "on the erased rows")},
+                              "full_buffer_kernels": (
+                                  "encode 3 transform passes; decode 7 (row scaling, 4 transform passes, 2 "
+                                  "derivative passes) plus the division on the erased rows"
+                                  if kinds["deriv"]["launches"] else
+                                  "one fused launch per encode and per decode (after the locator): the "
+                                  "transforms fit one tile, nothing goes through scratch")},
         "latency_ms": {"encode_p50": round(pct(enc_ms, 50), 4), "encode_p99": round(pct(enc_ms, 99), 4),
                        "decode_p50": round(pct(dec_ms, 50), 4), "decode_p99": round(pct(dec_ms, 99), 4)},
         "kernels": {kk: {"launches": v["launches"], "ms": round(v["ms"], 4),
