@@ -296,14 +296,20 @@ def run_ours(args):
     alu_peak = alu_peak_gmuls(sm_mhz, sms)
     achieved_mul = d["mults"] / (d["ms"] / 1e3) / 1e9 if d["ms"] else 0.0
     achieved_gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] else 0.0
-    roofline = {"bound": "alu", "kernel": "k_pass (transform butterfly pass)", "achieved": round(achieved_mul, 2),
+    fused = kinds["deriv"]["launches"] == 0  # short codewords: one launch per encode / decode
+    roofline = {"bound": "alu",
+                "kernel": ("k_fused_enc / k_fused_dec (whole algorithm per launch)" if fused
+                           else "k_pass (transform butterfly pass)"),
+                "achieved": round(achieved_mul, 2),
                 "peak": round(alu_peak, 2), "unit": "Gmul/s", "frac": round(achieved_mul / alu_peak, 4),
                 "peak_source": (f"derived: {sms} SMs x 64 ALU lanes/clk x {sm_mhz:.0f} MHz / 8.5 ALU ops per "
                                 "GF(2^16) split-table multiply-add"),
                 "alu_pipe": {"peak_tops": round(sms * 64 * sm_mhz * 1e6 / 1e12, 2), "ops_per_mult": 8.5,
                              "achieved_tops": round(achieved_mul * 8.5 / 1e3, 2)},
-                "traffic": KPASS_TRAFFIC["bytes"], "traffic_alg_bytes": KPASS_TRAFFIC["alg_bytes"],
-                "traffic_launch": KPASS_TRAFFIC["launch"], "launches_per_step": d["launches"] / args.steps,
+                "traffic": None if fused else KPASS_TRAFFIC["bytes"],
+                "traffic_alg_bytes": None if fused else KPASS_TRAFFIC["alg_bytes"],
+                "traffic_launch": None if fused else KPASS_TRAFFIC["launch"],
+                "launches_per_step": d["launches"] / args.steps,
                 "share_of_kernel_time": round(d["ms"] / tot_ms, 4) if tot_ms else None,
                 "hbm": {"achieved": round(achieved_gbs, 2), "peak": hbm, "unit": "GB/s",
                         "frac": round(achieved_gbs / hbm, 4), "peak_source": f"{hbm_src} hbm_gbs"}}
