@@ -1296,6 +1296,35 @@ template <int INV, class Mid>
 __device__ __forceinline__ void tile_levels_e(uint32_t sdata, uint32_t stab, uint32_t nlev, uint32_t lg_w,
                                               const ERowArgs &ra, Mid mid)
 {
+    if (nlev == 8 && (lg_w == 5 || lg_w == 4)) {
+        // 256-row tiles of 32 or 16 words: every shift and stride a constant
+        if (lg_w == 5) {
+            if (INV) {
+                eround_q<INV, 4, false, ER_PI>(sdata, stab, 255, 256, 5, 0, ra);
+                __syncthreads();
+                mid();
+                eround_q<INV, 4, true, ER_NONE>(sdata, stab, 255, 256, 5, 4, ra);
+            } else {
+                eround_q<INV, 4, true, ER_NONE>(sdata, stab, 255, 256, 5, 4, ra);
+                mid();
+                __syncthreads();
+                eround_q<INV, 4, false, ER_OUT>(sdata, stab, 255, 256, 5, 0, ra);
+            }
+        } else {
+            if (INV) {
+                eround_q<INV, 4, false, ER_PI>(sdata, stab, 255, 256, 4, 0, ra);
+                __syncthreads();
+                mid();
+                eround_q<INV, 4, true, ER_NONE>(sdata, stab, 255, 256, 4, 4, ra);
+            } else {
+                eround_q<INV, 4, true, ER_NONE>(sdata, stab, 255, 256, 4, 4, ra);
+                mid();
+                __syncthreads();
+                eround_q<INV, 4, false, ER_OUT>(sdata, stab, 255, 256, 4, 0, ra);
+            }
+        }
+        return;
+    }
     const uint32_t nrows = 1u << nlev, nrec = nrows - 1;
     const uint32_t qa = nlev <= 4 ? nlev : (nlev + 1) / 2, qb = nlev - qa;
     if (INV) {
@@ -1455,14 +1484,30 @@ __global__ void __launch_bounds__(NT, 1) k_fused_dec(FusedDecArgs a, uint32_t lg
         }
         cp_async_wait_all();
         __syncthreads();
-        tile_rows_mul<R>(s0, sr, n, lg_w); // u = B . phi
+        // 256-row tiles of 32 or 16 words (the widest slices fit for n = 256)
+        // take these steps with every shift and stride a constant
+        const bool c5 = n == 256 && lg_w == 5, c4 = n == 256 && lg_w == 4;
+        auto rows_mul = [&](uint32_t sd) {
+            if (c5)
+                tile_rows_mul<R>(sd, sr, 256, 5);
+            else if (c4)
+                tile_rows_mul<R>(sd, sr, 256, 4);
+            else
+                tile_rows_mul<R>(sd, sr, n, lg_w);
+        };
+        rows_mul(s0); // u = B . phi
         __syncthreads();
         stage_rows_recs(a.binvrec);
         cp_async_commit();
-        tile_nbr_sums<R>(s0, s1, lgn, lg_w);
+        if (c5)
+            tile_nbr_sums<R>(s0, s1, 8, 5);
+        else if (c4)
+            tile_nbr_sums<R>(s0, s1, 8, 4);
+        else
+            tile_nbr_sums<R>(s0, s1, lgn, lg_w);
         cp_async_wait_all();
         __syncthreads();
-        tile_rows_mul<R>(s1, sr, n, lg_w); // the derivative's coefficients, B^-1 (sums)
+        rows_mul(s1); // the derivative's coefficients, B^-1 (sums)
         __syncthreads();
         // while the forward transform runs on t1: the records of Pi | 1/Pi'
         // (this slice's last step and the next slice's first) and the next
