@@ -406,10 +406,10 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(PassArgs a, uint32_t l
 // the whole CTA meets where factor records change hands (its first item and
 // every new group), because all of its threads copy the records in.
 template <int R, int INV, int RB, bool SPLIT>
-__device__ __forceinline__ void pass_items(const PassArgs &a, uint32_t lg_cw, uint32_t ntiles, uint32_t i0, uint32_t i1,
-                                           uint8_t *sm)
+__device__ __forceinline__ void pass_items(const PassArgs &a, uint32_t nlev, uint32_t lg_cw, uint32_t ntiles,
+                                           uint32_t i0, uint32_t i1, uint8_t *sm)
 {
-    const uint32_t nlev = a.nlev, nrows = 1u << nlev, nrec = nrows - 1;
+    const uint32_t nrows = 1u << nlev, nrec = nrows - 1;
     const uint32_t tab_sz = tab_bytes<R>(nrec);
     const uint32_t stab0 = (uint32_t)__cvta_generic_to_shared(sm);
     const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
@@ -495,7 +495,14 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_p(PassArgs a, uint32_t
     const uint32_t i0 = (uint32_t)((uint64_t)blockIdx.x * items / gridDim.x);
     const uint32_t i1 = (uint32_t)((uint64_t)(blockIdx.x + 1) * items / gridDim.x);
     pdl_trigger();
-    pass_items<R, INV, RB, SPLIT>(a, lg_cw, ntiles, i0, i1, sm);
+    // The tuned plans of the large transforms (8 levels on 256-byte tiles, 7
+    // levels on 512-byte tiles) run with every shift and stride a constant.
+    if (a.nlev == 8 && lg_cw == 8)
+        pass_items<R, INV, RB, SPLIT>(a, 8, 8, ntiles, i0, i1, sm);
+    else if (a.nlev == 7 && lg_cw == 9)
+        pass_items<R, INV, RB, SPLIT>(a, 7, 9, ntiles, i0, i1, sm);
+    else
+        pass_items<R, INV, RB, SPLIT>(a, a.nlev, lg_cw, ntiles, i0, i1, sm);
 }
 
 // Algorithm 1's middle two passes in one (n = 2k, one coset): the tile holds
@@ -533,14 +540,10 @@ __device__ __forceinline__ void fused_coset_tile(uint32_t sdata, uint32_t stab, 
 // a.L0 + a.nlev = lg k, a.src = the k-row scratch, a.dst = the codeword,
 // fuse_k = k.
 template <int R, bool SPLIT>
-__global__ void __launch_bounds__(kPassThreads, 1) k_pass_cos(PassArgs a, uint32_t lg_cw, uint32_t ntiles,
-                                                              uint32_t items, uint32_t fuse_k)
+__device__ __forceinline__ void pass_cos_items(const PassArgs &a, uint32_t nlev, uint32_t lg_cw, uint32_t ntiles,
+                                               uint32_t i0, uint32_t i1, uint32_t fuse_k, uint8_t *sm)
 {
-    extern __shared__ __align__(128) uint8_t sm[];
-    const uint32_t i0 = (uint32_t)((uint64_t)blockIdx.x * items / gridDim.x);
-    const uint32_t i1 = (uint32_t)((uint64_t)(blockIdx.x + 1) * items / gridDim.x);
-    pdl_trigger();
-    const uint32_t nlev = a.nlev, nrows = 1u << nlev, nrec = nrows - 1;
+    const uint32_t nrows = 1u << nlev, nrec = nrows - 1;
     const uint32_t tab_sz = tab_bytes<R>(nrec);
     const uint32_t stab0 = (uint32_t)__cvta_generic_to_shared(sm);
     const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
@@ -589,6 +592,22 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_cos(PassArgs a, uint32
     }
     cp_async_wait_all();
     __syncthreads();
+}
+
+template <int R, bool SPLIT>
+__global__ void __launch_bounds__(kPassThreads, 1) k_pass_cos(PassArgs a, uint32_t lg_cw, uint32_t ntiles,
+                                                              uint32_t items, uint32_t fuse_k)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
+    const uint32_t i0 = (uint32_t)((uint64_t)blockIdx.x * items / gridDim.x);
+    const uint32_t i1 = (uint32_t)((uint64_t)(blockIdx.x + 1) * items / gridDim.x);
+    pdl_trigger();
+    // the tuned plan of the large encoder (8 levels on 256-byte tiles) with
+    // every shift and stride a constant
+    if (a.nlev == 8 && lg_cw == 8)
+        pass_cos_items<R, SPLIT>(a, 8, 8, ntiles, i0, i1, fuse_k, sm);
+    else
+        pass_cos_items<R, SPLIT>(a, a.nlev, lg_cw, ntiles, i0, i1, fuse_k, sm);
 }
 
 __global__ void __launch_bounds__(kThreads) k_superset(SupersetArgs a, uint32_t lg_cw)
