@@ -765,17 +765,17 @@ __device__ __forceinline__ void deriv_round(const DerivArgs &a, uint32_t su, uin
 // words per thread (every thread busy in a 4-bit round), else rounds of at
 // most 3 bits.
 template <int R, int MODE>
-__device__ __forceinline__ void deriv_tile(const DerivArgs &a, uint32_t su, uint32_t sacc, uint32_t s_b,
+__device__ __forceinline__ void deriv_tile(const DerivArgs &a, uint32_t nlev, uint32_t su, uint32_t sacc, uint32_t s_b,
                                            uint32_t s_binv, uint32_t lg_w, uint32_t hibase, uint32_t lo, size_t col,
                                            uint32_t width)
 {
     constexpr bool kX = MODE == 1, kInv = MODE != 0, kMulB = MODE != 1, kUout = MODE == 0;
-    const uint32_t nrows = 1u << a.nlev;
+    const uint32_t nrows = 1u << nlev;
     const bool wide = (nrows << lg_w) >= 16u * blockDim.x;
 #define LCH_DR(Q, S0, F, L, X, I)                                                                 \
     deriv_round<R, Q, S0, F, L, X, I, kMulB, kUout>(a, su, sacc, s_b, s_binv, nrows, lg_w, hibase, lo, col, width)
 #define LCH_SYNC __syncthreads()
-    switch (a.nlev) {
+    switch (nlev) {
     case 1: LCH_DR(1, 0, true, true, kX, kInv); break;
     case 2: LCH_DR(2, 0, true, true, kX, kInv); break;
     case 3: LCH_DR(3, 0, true, true, kX, kInv); break;
@@ -906,7 +906,7 @@ __device__ __forceinline__ void deriv_body(const DerivArgs &a, uint32_t lg_cw, u
         __syncthreads();
         if (t + 1 < ntiles) issue(t + 1, stage0 + ((t + 1) & 1u) * stage_bytes);
         cp_async_commit();
-        deriv_tile<R, MODE>(a, su, sacc, s_b, s_binv, lg_w, hibase, lo, col, width);
+        deriv_tile<R, MODE>(a, nlev, su, sacc, s_b, s_binv, lg_w, hibase, lo, col, width);
     }
     cp_async_wait_all();
     __syncthreads();
@@ -928,12 +928,12 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_deriv(DerivArgs a, uint32_t
 // X (which becomes the accumulator) into two slots.  (An L2 prefetch of the
 // next item beyond those in flight made both modes slower.)
 template <int R, int MODE>
-__device__ __forceinline__ void deriv_items(const DerivArgs &a, uint32_t lg_cw, uint32_t ntiles, uint32_t i0, uint32_t i1,
-                                            uint8_t *sm)
+__device__ __forceinline__ void deriv_items(const DerivArgs &a, uint32_t nlev, uint32_t lg_cw, uint32_t ntiles,
+                                            uint32_t i0, uint32_t i1, uint8_t *sm)
 {
     constexpr bool kX = MODE == 1, kMulB = MODE != 1;
     constexpr uint32_t kRing = kX ? 2 : 3;
-    const uint32_t nlev = a.nlev, nrows = 1u << nlev;
+    const uint32_t nrows = 1u << nlev;
     const uint32_t cw = 1u << lg_cw, lg_w = lg_cw - 2, lg_vpr = lg_cw - 4;
     const uint32_t rec_bytes = tab_bytes<R>(nrows);
     const uint32_t s_b = (uint32_t)__cvta_generic_to_shared(sm);
@@ -1008,7 +1008,7 @@ __device__ __forceinline__ void deriv_items(const DerivArgs &a, uint32_t lg_cw, 
         if (k != i0 && t == 0) __syncthreads();
         const size_t col = (size_t)t << lg_cw;
         const size_t rem = a.S - col;
-        deriv_tile<R, MODE>(a, su, sacc, s_b, s_binv, lg_w, hibase, lo, col, rem < cw ? (uint32_t)rem : cw);
+        deriv_tile<R, MODE>(a, nlev, su, sacc, s_b, s_binv, lg_w, hibase, lo, col, rem < cw ? (uint32_t)rem : cw);
     }
     cp_async_wait_all();
     __syncthreads();
@@ -1021,7 +1021,12 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_deriv_p(DerivArgs a, uint32
     const uint32_t i0 = (uint32_t)((uint64_t)blockIdx.x * items / gridDim.x);
     const uint32_t i1 = (uint32_t)((uint64_t)(blockIdx.x + 1) * items / gridDim.x);
     pdl_trigger();
-    deriv_items<R, MODE>(a, lg_cw, ntiles, i0, i1, sm);
+    // the large decoder's groups (8 levels on 128-byte tiles) with every
+    // shift and stride a constant
+    if (a.nlev == 8 && lg_cw == 7)
+        deriv_items<R, MODE>(a, 8, 7, ntiles, i0, i1, sm);
+    else
+        deriv_items<R, MODE>(a, a.nlev, lg_cw, ntiles, i0, i1, sm);
 }
 
 // Per-row scaling dst[row] = coef[row] (.) src[row] for kRowsPerCta rows per
