@@ -1586,10 +1586,9 @@ __host__ __device__ __forceinline__ size_t fused_enc_smem(uint32_t lgk, uint32_t
 }
 
 template <int R>
-__global__ void __launch_bounds__(kPassThreads, 1) k_fused_enc(FusedEncArgs a, uint32_t lg_cw)
+__device__ __forceinline__ void fused_enc_body(const FusedEncArgs &a, uint32_t lgk, uint32_t lg_cw, uint8_t *sm)
 {
-    extern __shared__ __align__(128) uint8_t sm[];
-    const uint32_t lgk = a.lgk, k = 1u << lgk;
+    const uint32_t k = 1u << lgk;
     const uint32_t lg_w = lg_cw - 2, lg_vpr = lg_cw - 4, cw = 1u << lg_cw;
     const uint32_t ftab = tab_bytes<R>(k - 1), tile = k << lg_cw;
     uint8_t *fcos = sm + ftab;
@@ -1633,6 +1632,18 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_fused_enc(FusedEncArgs a, u
         pass_tile<R, 0>(sw, sc, lgk, lg_w, o, false, lanes_all(lg_w));
         __syncthreads();
     }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kPassThreads, 1) k_fused_enc(FusedEncArgs a, uint32_t lg_cw)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
+    // 128-row messages on 512-byte slices (the widest that fit) with every
+    // shift and stride a constant
+    if (a.lgk == 7 && lg_cw == 9)
+        fused_enc_body<R>(a, 7, 9, sm);
+    else
+        fused_enc_body<R>(a, a.lgk, lg_cw, sm);
 }
 
 uint32_t ilog2(uint64_t x)
