@@ -188,11 +188,19 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- our arm
 
+# ALU-pipe operations the transform pass spends per multiplied element:
+# sm__inst_executed_pipe_alu.sum x 32 / multiplies, counted by ncu on the
+# decoder's levels-0..7 pass of large_gf16 (a pass with no zero-factor
+# butterflies), the butterfly XORs, index and loop arithmetic included.  The
+# multiply itself, on a packed pair of elements, is 12 index ops, 4 combines
+# and 1 XOR: 8.5 per element before the pass's constant shifts and strides.
+ALU_OPS_PER_MULT = 7.96
+
+
 def alu_peak_gmuls(sm_mhz, sms):
-    """Integer-pipe ceiling of the split-table GF(2^16) multiply-add: each pair
-    of packed elements needs 12 index ops (shift, mask|base), 4 combines and 1
-    XOR on the 64-lane ALU pipe, i.e. 8.5 ALU ops per element."""
-    return sms * 64 * sm_mhz * 1e6 / 8.5 / 1e9
+    """Integer-pipe ceiling of the split-table GF(2^16) transform: the 64-lane
+    ALU pipe of every SM at the sampled clock over ALU_OPS_PER_MULT."""
+    return sms * 64 * sm_mhz * 1e6 / ALU_OPS_PER_MULT / 1e9
 
 
 def pct(xs, q):
@@ -302,10 +310,11 @@ def run_ours(args):
                            else "k_pass (transform butterfly pass)"),
                 "achieved": round(achieved_mul, 2),
                 "peak": round(alu_peak, 2), "unit": "Gmul/s", "frac": round(achieved_mul / alu_peak, 4),
-                "peak_source": (f"derived: {sms} SMs x 64 ALU lanes/clk x {sm_mhz:.0f} MHz / 8.5 ALU ops per "
-                                "GF(2^16) split-table multiply-add"),
-                "alu_pipe": {"peak_tops": round(sms * 64 * sm_mhz * 1e6 / 1e12, 2), "ops_per_mult": 8.5,
-                             "achieved_tops": round(achieved_mul * 8.5 / 1e3, 2)},
+                "peak_source": (f"derived: {sms} SMs x 64 ALU lanes/clk x {sm_mhz:.0f} MHz / {ALU_OPS_PER_MULT} "
+                                "ALU ops per multiplied element (ncu-counted in the transform pass)"),
+                "alu_pipe": {"peak_tops": round(sms * 64 * sm_mhz * 1e6 / 1e12, 2),
+                             "ops_per_mult": ALU_OPS_PER_MULT,
+                             "achieved_tops": round(achieved_mul * ALU_OPS_PER_MULT / 1e3, 2)},
                 "traffic": None if fused else KPASS_TRAFFIC["bytes"],
                 "traffic_alg_bytes": None if fused else KPASS_TRAFFIC["alg_bytes"],
                 "traffic_launch": None if fused else KPASS_TRAFFIC["launch"],
