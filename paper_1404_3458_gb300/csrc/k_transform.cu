@@ -1408,15 +1408,12 @@ __device__ __forceinline__ DecSlice dec_slice(uint32_t y, uint32_t lg_cw, uint32
     return {((size_t)nfull << lg_cw) + ((size_t)(y - nfull) << (lg_cw - 1)), lg_cw - 1};
 }
 
-// NT threads: 1024 when a slice has at least 4096 words (32 warps hide the
-// barriers between the decode's many short phases better: medium_gf16 96 us
-// against 102 at 512), else 512.
-template <int R, int NT>
-__global__ void __launch_bounds__(NT, 1) k_fused_dec(FusedDecArgs a, uint32_t lg_cw, uint32_t nfull, uint32_t nitems)
+template <int R>
+__device__ __forceinline__ void fused_dec_body(const FusedDecArgs &a, uint32_t lgn, uint32_t lg_cw, uint32_t nfull,
+                                               uint32_t nitems, uint8_t *sm)
 {
-    extern __shared__ __align__(128) uint8_t sm[];
     constexpr uint32_t cpr = FT<R>::rec_bytes / 16;
-    const uint32_t lgn = a.lgn, n = 1u << lgn;
+    const uint32_t n = 1u << lgn;
     uint8_t *rrec = sm + tab_bytes<R>(n - 1);
     uint8_t *t0 = rrec + tab_bytes<R>(n);
     uint8_t *t1 = t0 + (n << lg_cw);
@@ -1563,6 +1560,21 @@ __global__ void __launch_bounds__(NT, 1) k_fused_dec(FusedDecArgs a, uint32_t lg
         }
         y = ynext;
     }
+}
+
+// NT threads: 1024 when a slice has at least 4096 words (32 warps hide the
+// barriers between the decode's many short phases better: medium_gf16 96 us
+// against 102 at 512), else 512.
+template <int R, int NT>
+__global__ void __launch_bounds__(NT, 1) k_fused_dec(FusedDecArgs a, uint32_t lg_cw, uint32_t nfull, uint32_t nitems)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
+    // 256-row codewords on 128-byte slices (the widest that fit) with every
+    // shift and stride that does not depend on the slice a constant
+    if (a.lgn == 8 && lg_cw == 7)
+        fused_dec_body<R>(a, 8, 7, nfull, nitems, sm);
+    else
+        fused_dec_body<R>(a, a.lgn, lg_cw, nfull, nitems, sm);
 }
 
 // ------------------------------------------------ fused encode of short messages
